@@ -1,0 +1,133 @@
+"""Pins of the oracle's time integration (central difference, lumped mass; paper Sec. 3, Sec. 4)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_13190_gb300 import specimen, workloads
+from paper_2603_13190_gb300.specimen import Specimen
+from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
+
+MAT = dict(WORKLOAD_MATERIAL)
+EL = dict(WORKLOAD_MATERIAL, elastic=1)
+
+
+def two_particle(l=3.0, a0=2.0):
+    """Particles I at the origin and J at (l, 0, 0) sharing one square-ish facet in the mid plane."""
+    x = np.array([[0.0, 0.0, 0.0], [l, 0.0, 0.0]])
+    h = math.sqrt(2 * a0)  # right triangle with legs h: area a0
+    vtx = np.array([[l / 2, -h / 3, -h / 3, l / 2, 2 * h / 3, -h / 3, l / 2, -h / 3, 2 * h / 3]])
+    return Specimen(x=x, diameter=np.array([1.0, 1.0]), tets=np.zeros((0, 4), np.int32),
+                    facet_pi=np.array([0], np.int32), facet_pj=np.array([1], np.int32),
+                    facet_tet=np.array([-1], np.int32), facet_vtx=vtx, edge=l, d_min=1.0, d_max=1.0)
+
+
+def test_two_particle_stiffness_and_lambda_max_closed_form():
+    """One facet between two nodes, centroid on the mid plane at the axis: axial stiffness A E0 / l,
+    shear stiffness A alpha E0 / l acting on g = (-1, -l/2, 1, -l/2) over (u_Iy, th_Iz, u_Jy, th_Jz).
+    Largest eigenvalue of M^-1 K = max(2 k_a / m, k_s (2/m + l^2 / (2 I)))."""
+    l, a0, m, I = 3.0, 2.0, 1e-6, 2e-7
+    spec = two_particle(l, a0)
+    o = oracle.Oracle(spec, MAT, 1e-7, mass=np.full(2, m), inertia=np.full((2, 3), I))
+    A = o.geometry()["area"][0]
+    assert abs(A - a0) < 1e-12
+    ka, ks = A * MAT["E0"] / l, A * MAT["alpha"] * MAT["E0"] / l
+    q = np.zeros((2, 6))
+    q[1, 0] = 1e-3  # pull J along the axis
+    f = o.elastic_force(q)
+    np.testing.assert_allclose(f[:, 0], [ka * 1e-3, -ka * 1e-3], rtol=1e-12)
+    q = np.zeros((2, 6))
+    q[1, 1] = 1e-3  # slide J sideways: shear force and the moments of a lever l/2 on each side
+    f = o.elastic_force(q)
+    np.testing.assert_allclose(f[:, 1], [ks * 1e-3, -ks * 1e-3], rtol=1e-12)
+    np.testing.assert_allclose(f[:, 5], [ks * 1e-3 * l / 2, ks * 1e-3 * l / 2], rtol=1e-12)
+    lam = max(2 * ka / m, ks * (2 / m + l * l / (2 * I)))
+    x0 = np.random.default_rng(0).standard_normal(12)
+    assert abs(o.lambda_max(x0, 400) - lam) < 1e-9 * lam
+
+
+def test_two_particle_axial_oscillation_period():
+    """Axial vibration of the 2-node system: central difference with dt << T reproduces the period
+    2 pi / omega, omega^2 = k_a (1/m_I + 1/m_J) (relative motion of two masses on a spring)."""
+    l, a0, m = 3.0, 2.0, 1e-6
+    spec = two_particle(l, a0)
+    ka = a0 * EL["E0"] / l
+    w = math.sqrt(ka * 2 / m)
+    T = 2 * math.pi / w
+    dt = T / 2000
+    bc = workloads.free_bc(2)
+    bc.v0[0, 0], bc.v0[1, 0] = -1.0, 1.0
+    o = oracle.Oracle(spec, EL, dt, bc, mass=np.full(2, m), inertia=np.full((2, 3), 1e-7))
+    gap = []
+    for _ in range(2000):
+        o.step(1)
+        q, _, _, _ = o.get_state()
+        gap.append(q[1, 0] - q[0, 0])
+    gap = np.array(gap)
+    # relative displacement 2 v0 / w sin(w t): zero crossing at half period, amplitude 2/w
+    k = int(np.argmax(gap < 0))
+    assert abs(k - 1000) <= 2
+    assert abs(gap.max() - 2.0 / w) < 1e-5 * (2.0 / w)
+
+
+def test_elastic_vibration_conserves_energy():
+    """Workload 'elastic_vibration' (Sec. 4.1 stand-in): 2000 steps at 0.9 dt_crit, energy error
+    below 1 % (free vibration: W_ext = 0, W_kin + W_int stays at W_kin0)."""
+    wl = workloads.WORKLOADS["elastic_vibration"]
+    spec = wl.specimen()
+    bc = workloads.workload_bc(wl.name, spec)
+    o = oracle.Oracle(spec, wl.material, 1e-7, bc)
+    dt = wl.dt_factor * o.critical_dt()
+    o = oracle.Oracle(spec, wl.material, dt, bc)
+    o.step(wl.steps)
+    (Wext, Wint, Wkin, err), _ = o.energy()
+    assert Wext == 0.0
+    assert err < 1.0
+    assert Wint > 0.05 * Wkin  # energy really moved between kinetic and stored
+
+
+def test_free_flight_conserves_momentum():
+    """With no constraints the internal forces cannot change total linear or angular momentum."""
+    spec = specimen.make_cube_specimen(10.0, 2.0, 4.0, 100, seed=11)
+    rng = np.random.default_rng(1)
+    bc = workloads.free_bc(spec.n_particles)
+    bc.v0[:] = rng.standard_normal(bc.v0.shape) * 5.0
+    o = oracle.Oracle(spec, MAT, 1e-7, bc)
+    o = oracle.Oracle(spec, MAT, 0.9 * o.critical_dt(), bc)
+    m6 = o.geometry()["mass"]
+
+    def momenta():
+        q, v, _, _ = o.get_state()
+        p = (m6[:, :3] * v[:, :3]).sum(0)
+        xq = spec.x + q[:, :3]
+        L = (np.cross(xq, m6[:, :3] * v[:, :3]) + m6[:, 3:] * v[:, 3:]).sum(0)
+        return p, L
+
+    p0, L0 = momenta()
+    o.step(300)
+    p1, L1 = momenta()
+    assert np.abs(p1 - p0).max() < 1e-10 * np.abs(m6[:, 0] * 5).sum()
+    # small-rotation kinematics: angular momentum holds to first order in the displacements
+    assert np.abs(L1 - L0).max() < 1e-2 * np.abs(L0).max()
+
+
+@pytest.mark.parametrize("steps", [1500])
+def test_tension_energy_balance_through_softening(steps):
+    """Uniaxial tension to post-peak on a small cube: the energy balance error of Sec. 4 stays below 1 %
+    and the macroscopic stress rises, peaks and softens."""
+    spec = specimen.make_cube_specimen(10.0, 2.0, 4.0, 220, seed=3)
+    bc = workloads.uniaxial_tension_bc(spec, velocity=50.0, ramp_time=1e-5)
+    o = oracle.Oracle(spec, MAT, 1e-7, bc)
+    dt = 0.9 * o.critical_dt()
+    o = oracle.Oracle(spec, MAT, dt, bc)
+    stress = []
+    for _ in range(steps // 10):
+        o.step(10)
+        (Wext, Wint, Wkin, err), R = o.energy()
+        stress.append(R[8] / spec.edge ** 2)  # reaction on the prescribed u_z DOFs, over the area
+    stress = np.array(stress)
+    k = int(np.argmax(stress))
+    assert 0 < k < len(stress) - 3, "peak must lie inside the run"
+    assert stress[-1] < 0.7 * stress[k]
+    assert err < 1.0
