@@ -1,0 +1,379 @@
+#!/usr/bin/env python3
+"""Benchmark: facet-updates/s of the LDPM explicit central-difference step on GB300, mixed vs FP64.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One "step" is one explicit central-difference step of the whole specimen (half kick and drift, facet
+pass, particle pass).  The default workload is the uniaxial-tension cube (50 mm, d = 2..4 mm,
+~1.8M facets) in mixed precision (FP32 facets, FP64 particle state); the same workload is also
+measured in FP64.  L2 is flushed (a 512 MB write) before every timed step and the flush is outside
+the timed intervals.  With --gpus N > 1 (torchrun) every rank steps its own replica of the specimen
+(the explicit step has no exchange between independent specimens: weak scaling, replicas only).
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "facet-updates/s per explicit step and % of HBM roofline, mixed vs FP64"
+UNIT = "facet-updates/s"
+
+# Algorithmic bytes per facet of the facet pass (values the method must read or write once per
+# step): geometry c_a + A, history read + write, facet force (3 values), tetrahedron ids / 12, and the
+# vertex records x, q, v (15 doubles) once per particle.
+def facet_pass_bytes(F: int, T: int, N: int, r: int) -> float:
+    return F * (4 * r + 8 * r + 3 * r) + T * 16 + N * 120
+
+
+def gather_pass_bytes(F: int, N: int, r: int) -> float:
+    # two facet ends per facet: arm (3 r) + id (r) and the facet force (3 r) each; per particle the
+    # row pointer, q and v read and written, forces and energy sums read and written, constants read.
+    return F * 2 * (4 * r + 3 * r) + N * (4 + 96 + 96 + 64 + 64 + 64)
+
+
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("ldpm_kernels.cu", "ldpm_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy burst)"
+    return 6800.0, "fallback (6.8 TB/s)"
+
+
+def recorded_traffic(kernel: str, workload: str, prec: str):
+    """DRAM bytes per launch from a committed ncu summary, valid only for the kernel source it was
+    taken from (null otherwise)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        e = d.get("%s/%s/%s" % (kernel, workload, prec))
+        if e and e.get("kernel_src_hash") == kernel_src_hash():
+            return float(e["bytes_per_launch"])
+    except Exception:
+        return None
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            if len(r) >= 9:
+                for k, nm in enumerate(names):
+                    if r[5 + k].lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        import torch
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def barrier_max(world: int, value: float) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def make_inputs(workload: str):
+    from paper_2603_13190_gb300 import workloads
+
+    wl = workloads.WORKLOADS[workload]
+    spec = wl.specimen()
+    bc = workloads.workload_bc(workload, spec)
+    return wl, spec, bc
+
+
+def time_steps(model, ldpm, torch, stream, flush, steps: int, warmup: int, profile: bool):
+    """Per-step device time (CUDA events on the library's stream), L2 flushed before every step."""
+    for _ in range(warmup):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        model.step(1)
+    stream.synchronize()
+    if profile:
+        ldpm.ldpm_profile(model.h, True)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for a, b in ev:
+        with torch.cuda.stream(stream):
+            flush.zero_()
+            a.record(stream)
+        model.step(1)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    kern = None
+    if profile:
+        kms, kcnt = ldpm.ldpm_profile_read(model.h)
+        ldpm.ldpm_profile(model.h, False)
+        kern = {"kick": (kms[0], int(kcnt[0])), "facet": (kms[1], int(kcnt[1])), "gather": (kms[2], int(kcnt[2]))}
+    return ms, kern
+
+
+def run_ours(args, rank, world, local):
+    import torch
+
+    from paper_2603_13190_gb300 import ldpm
+
+    torch.cuda.set_device(local)
+    wl, spec, bc = make_inputs(args.workload)
+    N, T, F = spec.n_particles, spec.n_tets, spec.n_facets
+    stream = torch.cuda.Stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peak, peak_src = measured_peaks()
+    out = {}
+    dt0 = None
+    for prec, steps in (("mixed", args.steps), ("fp64", max(3, args.steps // 4))):
+        model = ldpm.Model(spec, wl.material, precision=prec, dt=dt0 or 0.0, bc=bc, stream=stream, device=local)
+        dt0 = dt0 or model.dt
+        barrier(world)
+        torch.cuda.synchronize()
+        sampler = ClockSampler(local) if (rank == 0 and prec == "mixed") else None
+        if sampler:
+            sampler.__enter__()
+        ms, _ = time_steps(model, ldpm, torch, stream, flush, steps, args.warmup, profile=False)
+        if sampler:
+            sampler.__exit__()
+        torch.cuda.synchronize()
+        barrier(world)
+        tot = barrier_max(world, sum(ms))
+        # per-kernel durations from events around each launch (same stream), separate pass
+        _, kern = time_steps(model, ldpm, torch, stream, flush, steps, 1, profile=True)
+        r = 4 if prec == "mixed" else 8
+        fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(F, N, r)
+        facet_ms = kern["facet"][0] / max(1, kern["facet"][1])
+        gather_ms = kern["gather"][0] / max(1, kern["gather"][1])
+        achieved = fb / (facet_ms * 1e-3) / 1e9
+        # steady state: back-to-back steps from one captured graph, no flush (L2 may hold data)
+        model.step(args.warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nss = max(10, steps)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+        model.step(nss)
+        with torch.cuda.stream(stream):
+            e1.record(stream)
+        stream.synchronize()
+        ss_ms = e0.elapsed_time(e1) / nss
+        energy, _ = model.energy()
+        out[prec] = dict(
+            steps=steps, ms=ms, total_ms=tot, value=world * F * steps / (tot * 1e-3),
+            facet_ms=facet_ms, gather_ms=gather_ms, kick_ms=kern["kick"][0] / max(1, kern["kick"][1]),
+            roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                      "traffic": recorded_traffic("facet_kernel", args.workload, prec),
+                      "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
+            gather_roofline={"achieved": gb / (gather_ms * 1e-3) / 1e9, "frac": gb / (gather_ms * 1e-3) / 1e9 / peak,
+                             "algorithmic_bytes_per_launch": gb},
+            steady_state={"facet_updates_per_s": world * F / (ss_ms * 1e-3), "ms_per_step": ss_ms,
+                          "l2": "not flushed (graph replay, back-to-back)"},
+            energy_err_pct=float(energy[3]), clocks=sampler.summary() if sampler else None, dt=model.dt)
+        model.close()
+    # end to end through the C ABI with host buffers: create (H2D of the geometry), K steps each with an
+    # energy/reaction read-back (D2H), final state read-back, destroy.
+    barrier(world)
+    torch.cuda.synchronize()
+    K = args.steps
+    t0 = time.perf_counter()
+    m = ldpm.Model(spec, wl.material, precision="mixed", dt=dt0, bc=bc, device=local)
+    for _ in range(K):
+        m.step(1)
+        m.energy()
+    q, v, h5, _ = m.get_state()
+    m.close()
+    torch.cuda.synchronize()
+    e2e_s = barrier_max(world, time.perf_counter() - t0)
+    geo_bytes = spec.x.nbytes + spec.diameter.nbytes + spec.tets.nbytes + 3 * 4 * F + spec.facet_vtx.nbytes + \
+        bc.mask.nbytes + bc.vel.nbytes + bc.v0.nbytes
+    d2h = K * (16 * 8) + q.nbytes + v.nbytes + h5.nbytes
+    mx = out["mixed"]
+    res = {
+        "metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mx["total_ms"] / mx["steps"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
+                   "particles": N, "tets": T, "facets": F, "precision": "mixed: FP32 facet pass, FP64 particle state",
+                   "dt_s": dt0, "l2": "flushed (512 MB write) before every timed step, outside the timed interval",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "seed": wl.seed},
+        "roofline": mx["roofline"],
+        "gather_roofline": mx["gather_roofline"],
+        "kernel_ms": {"kick": mx["kick_ms"], "facet": mx["facet_ms"], "gather": mx["gather_ms"]},
+        "steady_state": mx["steady_state"],
+        "fp64": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["total_ms"] / out["fp64"]["steps"],
+                 "steps": out["fp64"]["steps"], "roofline": out["fp64"]["roofline"],
+                 "kernel_ms": {"kick": out["fp64"]["kick_ms"], "facet": out["fp64"]["facet_ms"],
+                               "gather": out["fp64"]["gather_ms"]},
+                 "steady_state": out["fp64"]["steady_state"]},
+        "mixed_over_fp64": mx["value"] / out["fp64"]["value"],
+        "e2e": {"value": world * F * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": geo_bytes / K,
+                "d2h_bytes_per_step": d2h / K, "seconds": e2e_s,
+                "what": "ldpm_create from host arrays, K x (ldpm_step(1) + ldpm_energy read-back), "
+                        "ldpm_get_state to host, ldpm_destroy"},
+        "gpu_launches": 3 * args.steps,
+        "clocks": mx["clocks"],
+    }
+    return res, spec, wl, bc, dt0
+
+
+def cpu_baseline(spec, wl, bc, dt, budget_s: float = 20.0):
+    """The FP64 oracle as it stands, single thread on the host, on a bounded sample of the workload."""
+    import oracle
+
+    o = oracle.Oracle(spec, wl.material, dt, bc)
+    o.step(1)
+    n, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and n < 200:
+        o.step(1)
+        n += 1
+    el = time.perf_counter() - t0
+    return {"value": spec.n_facets * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d explicit steps of the full %d-facet specimen (%.1f s, single thread)" % (n, spec.n_facets, el)}
+
+
+def run_reference(args, rank, world):
+    """The oracle as the reference arm: same workload, metric and unit, timed on the host cores."""
+    if rank != 0:
+        return None
+    import oracle
+
+    from paper_2603_13190_gb300 import workloads
+
+    wl, spec, bc = make_inputs(args.workload)
+    o = oracle.Oracle(spec, wl.material, 1e-7, bc)
+    x0 = np.random.default_rng(0).standard_normal(6 * spec.n_particles)
+    dt = wl.dt_factor * 2.0 / np.sqrt(o.lambda_max(x0, 200))
+    o = oracle.Oracle(spec, wl.material, dt, bc)
+    for _ in range(args.warmup):
+        o.step(1)
+    t = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        o.step(1)
+        t.append(time.perf_counter() - t0)
+    tot = sum(t)
+    val = spec.n_facets * args.steps / tot
+    return {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
+                       "particles": spec.n_particles, "tets": spec.n_tets, "facets": spec.n_facets,
+                       "precision": "FP64 oracle", "dt_s": dt, "seed": wl.seed},
+            "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": "%d full explicit steps after %d warm-up steps, single thread" %
+                                       (args.steps, args.warmup)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--workload", default="uniaxial_tension")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        world = int(os.environ.get("WORLD_SIZE", "1"))
+        res = run_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    rank, world, local = dist_setup(args.gpus)
+    res, spec, wl, bc, dt = run_ours(args, rank, world, local)
+    if rank == 0:
+        if world == 1 and not args.no_cpu_baseline:
+            res["cpu_baseline"] = cpu_baseline(spec, wl, bc, dt)
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

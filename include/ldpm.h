@@ -1,0 +1,193 @@
+/*
+ * ldpm.h -- C ABI of libldpm.so: the explicit central-difference time step of the Lattice Discrete
+ * Particle Model (LDPM) on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Method (arXiv 2603.13190, "LDPM: comparison of various time integration solvers and
+ * implementations"):
+ *   - facet strain from the rigid-body jump of the two particles, Sec. 2, Eq. (1);
+ *   - facet constitutive law t = T(e, s, p), Sec. 2 and Appendix A (fracture A.1, compression A.2,
+ *     friction A.3);
+ *   - particle force and moment balance, Sec. 2, Eq. (2a)-(2b), with the projected area A = A0 n.n0;
+ *   - M q'' + f_int(q) = f_ext with a lumped mass, integrated by the central-difference scheme of
+ *     the explicit solvers (Sec. 3, Sec. 3.2, the lumped-mass rule of Sec. 3.2.5);
+ *   - energy balance 100 |W_ext - W_int - W_kin| / W_ext, Sec. 4.
+ *
+ * Conventions shared by every entry point:
+ *   - Units are consistent; the library does not convert.  mm-N-MPa-tonne-s is recommended.
+ *   - Every function returns LDPM_OK (0) or a negative LDPM_E_* code; ldpm_last_error() then holds
+ *     a message for the calling thread.  No C++ exception crosses this boundary.
+ *   - Arrays passed in are host memory owned by the caller, read during the call and never kept.
+ *     Arrays passed out are host memory owned by the caller and written before the call returns.
+ *   - Device memory, streams and CUDA graphs are owned by the ldpm_t handle and released by
+ *     ldpm_destroy().
+ *   - Particle arrays use the caller's particle order; facet arrays use the caller's facet order
+ *     and orientation (force "on I" means on facet_pi[k]).  The library reorders internally.
+ *   - DOF order per particle: u_x, u_y, u_z, theta_x, theta_y, theta_z.
+ */
+#ifndef LDPM_H
+#define LDPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LDPM_OK 0
+#define LDPM_E_INVALID_ARG (-1)   /* a pointer, size or option is invalid */
+#define LDPM_E_BAD_GEOMETRY (-2)  /* geometry violates the mesh rules listed at ldpm_geometry */
+#define LDPM_E_CUDA (-3)          /* a CUDA call failed (message names it) */
+#define LDPM_E_OOM (-4)           /* device or host allocation failed */
+#define LDPM_E_UNSTABLE (-5)      /* a velocity or displacement became NaN/Inf (step too large?) */
+#define LDPM_E_TIMEOUT (-6)       /* a bounded device-side wait expired */
+#define LDPM_E_UNSUPPORTED (-7)   /* a parameter combination the library does not implement */
+
+typedef struct ldpm_ctx *ldpm_t; /* opaque handle, owned by the library */
+
+typedef enum {
+    LDPM_FP64 = 0,  /* every stage in FP64 */
+    LDPM_MIXED = 1  /* facet kinematics and constitutive law in FP32; particle state, velocity
+                       update, force sums and energies in FP64 */
+} ldpm_precision;
+
+/* Raw specimen geometry (paper Sec. 3.1: particles, Delaunay tetrahedra, 12 facets per
+ * tetrahedron).  Mesh rules checked by ldpm_create (LDPM_E_BAD_GEOMETRY otherwise):
+ *   - n_facets == 12 * n_tets, every tetrahedron has 4 distinct particles and nonzero volume;
+ *   - every facet belongs to facet_tet[k], its particles facet_pi[k] != facet_pj[k] are two
+ *     vertices of that tetrahedron, and each of the 6 tetrahedron edges carries exactly 2 facets;
+ *   - facet triangles have nonzero area; particle distances are nonzero and below l_t. */
+typedef struct {
+    int32_t n_particles, n_tets, n_facets;
+    const double *x;          /* [N][3] particle centres */
+    const double *diameter;   /* [N] particle diameters (0 allowed for surface nodes); may be NULL
+                                 only if `inertia` is given */
+    const int32_t *tet;       /* [T][4] particle indices of each tetrahedron */
+    const int32_t *facet_pi;  /* [F] particle I of facet k */
+    const int32_t *facet_pj;  /* [F] particle J of facet k; n_k points from I to J */
+    const int32_t *facet_tet; /* [F] tetrahedron owning facet k */
+    const double *facet_vtx;  /* [F][9] the three vertices of the facet triangle: its centroid is the
+                                 point the arms c_I, c_J reach; its area A0 and normal n0 give the
+                                 projected area A = A0 |n . n0| (Sec. 2) */
+    const double *mass;       /* [N] translational mass or NULL: tetrahedron mass rho V split
+                                 equally over its 4 nodes (Sec. 3.2.5) */
+    const double *inertia;    /* [N][3] diagonal rotary inertia or NULL: m d^2 / 10 (Sec. 3.2.5),
+                                 nodes with d = 0 take the smallest positive diameter */
+} ldpm_geometry;
+
+/* Material parameters, Appendix A table (names follow the paper's symbols). */
+typedef struct {
+    double rho;      /* density */
+    double E0;       /* effective normal modulus */
+    double alpha;    /* shear-normal coupling */
+    double sigma_t;  /* tensile strength */
+    double l_t;      /* tensile characteristic length, l_t = 2 E0 G_t / sigma_t^2 */
+    double r_st;     /* shear-to-tensile strength ratio sigma_s / sigma_t */
+    double n_t;      /* softening exponent */
+    double sigma_c0; /* compressive yielding strength */
+    double Hc0_E0;   /* initial hardening modulus ratio */
+    double Hc1_E0;   /* final hardening modulus ratio */
+    double kc0, kc1, kc2, kc3; /* kappa_c0..kappa_c3 */
+    double mu0, mu_inf;        /* initial and asymptotic friction */
+    double sigma_N0;           /* transitional stress */
+    double Ed_E0;              /* densification ratio (only 1 is supported) */
+    double beta;               /* volumetric-deviatoric coupling */
+    double k_t;                /* tensile unloading (only 0 is supported) */
+    double r_s;                /* shear softening modulus ratio (only 0 is supported) */
+    int32_t elastic;           /* 1: linear elastic facets t = E e (Sec. 2) */
+    int32_t reserved;          /* must be 0 */
+} ldpm_material;
+
+/* Boundary-condition codes per DOF (ldpm_options.bc_mask, ldpm_set_bc). */
+#define LDPM_BC_FREE 0
+#define LDPM_BC_FIXED 1      /* velocity 0 */
+#define LDPM_BC_VELOCITY 2   /* velocity bc_vel * ramp(t), ramp(t) = clamp(t / ramp_time, 0, 1),
+                                ramp = 1 when ramp_time <= 0 */
+
+typedef struct {
+    int32_t precision;   /* ldpm_precision */
+    int32_t graph_chunk; /* steps per captured CUDA graph in ldpm_step; 0 = 32; < 0: no graphs */
+    double dt;           /* time step; <= 0: dt_factor * 2 / sqrt(lambda_max(M^-1 K)), the largest
+                            eigenvalue found by power iteration on the elastic operator */
+    double dt_factor;    /* <= 0 means 0.9 (the paper runs at about 90 % of the critical step) */
+    void *cuda_stream;   /* cudaStream_t all work is enqueued on; NULL = a library-owned stream */
+    const int32_t *bc_mask; /* [N][6] LDPM_BC_* or NULL (all free) */
+    const double *bc_vel;   /* [N][6] prescribed velocities or NULL */
+    double ramp_time;       /* ramp duration of prescribed velocities */
+    const double *v0;       /* [N][6] initial velocity or NULL */
+    const double *f_ext;    /* [N][6] constant external nodal forces or NULL */
+    int32_t device;         /* CUDA device ordinal; < 0 = the current device */
+    int32_t reserved;       /* must be 0 */
+} ldpm_options;
+
+/* Create a specimen from raw geometry (copied).  Validates the mesh rules, derives facet frames,
+ * arms and projected areas, the lumped mass, the particle-to-facet CSR list and the Morton-ordered
+ * device layout, uploads, and estimates dt if not given.  Initial state: q = 0, v = v0 (fixed DOFs
+ * 0, prescribed DOFs at their prescribed velocity), zero facet history.  On success *out owns all
+ * device memory.  Errors: INVALID_ARG, BAD_GEOMETRY, UNSUPPORTED (k_t != 0, r_s != 0,
+ * Ed_E0 != 1), OOM, CUDA. */
+int ldpm_create(const ldpm_geometry *geom, const ldpm_material *mat, const ldpm_options *opt, ldpm_t *out);
+
+/* Enqueue nsteps central-difference steps (Sec. 3) on the handle's stream and return without
+ * waiting.  Each step: half kick and drift of every particle (prescribed DOFs follow their
+ * velocity), then per facet the strain of Eq. (1), the Appendix A law and the force A P t, then the
+ * per-particle sums of Eq. (2) in a fixed order, the second half kick and the energy increments.
+ * nsteps == 0 is a no-op.  Errors: INVALID_ARG (nsteps < 0), CUDA. */
+int ldpm_step(ldpm_t h, int64_t nsteps);
+
+/* Wait for all work enqueued on the handle's stream.  Returns UNSTABLE if a step produced a
+ * non-finite velocity or displacement. */
+int ldpm_sync(ldpm_t h);
+
+/* Copy the state out (synchronises).  q, v: [N][6]; hist5: [F][5] per facet t_N, the tangential
+ * traction t_M m + t_L l as a global 3-vector, e_max (the traction acting on facet_pi[k]); step: the
+ * step counter.  Any pointer may be NULL.  Returns UNSTABLE after a non-finite state (data still
+ * copied). */
+int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step);
+
+/* Replace the state (synchronises).  Same layouts as ldpm_get_state; hist5 may be NULL (zero
+ * history).  The internal forces of the new state are rebuilt from the given tractions; energy
+ * accumulators restart (W_ext = W_int = 0, W_kin0 = kinetic energy of v). */
+int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *hist5, int64_t step);
+
+/* Energies and reactions of the current state (synchronises).  out = {W_ext, W_int, W_kin, err%}
+ * with err% = 100 |W_ext + W_kin0 - W_int - W_kin| / (|W_ext| + W_kin0) (Sec. 4; W_kin0 = 0 in the
+ * loaded tests makes it the paper's formula).  reaction[12] (may be NULL): sums over fixed DOFs of
+ * the force the supports apply, per DOF component (6), then the same over velocity-prescribed DOFs
+ * (6). */
+int ldpm_energy(ldpm_t h, double out[4], double reaction[12]);
+
+/* Forces of the current state (synchronises): F3 [F][3] facet force A P t acting on facet_pi[k];
+ * f6 [N][6] per-particle sums of facet forces and moments.  Either pointer may be NULL. */
+int ldpm_facet_forces(ldpm_t h, double *F3, double *f6);
+
+/* Replace the boundary conditions (takes effect for steps enqueued afterwards).  mask [N][6],
+ * vel [N][6] (NULL = zeros), ramp measured from t = 0. */
+int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_time);
+
+/* Sizes and step: info[0..4] = N, T, F, precision, step counter (synchronises); *dt = time step. */
+int ldpm_info(ldpm_t h, int64_t info[5], double *dt);
+
+/* Per-kernel CUDA-event timing of ldpm_step on the handle's stream.  enable = 1 starts (and
+ * clears) recording, 0 stops.  ldpm_profile_read fills ms[k] (summed milliseconds) and count[k]
+ * (launches) for k = 0 kick, 1 facet pass, 2 gather+update; n = entries the caller provides. */
+int ldpm_profile(ldpm_t h, int32_t enable);
+int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n);
+
+/* Checkpoint of the complete mutable state in the library's internal layout (bitwise resume).
+ * ldpm_checkpoint_size gives the byte count; save/load copy through caller host memory and
+ * synchronise. */
+int64_t ldpm_checkpoint_size(ldpm_t h);
+int ldpm_save_checkpoint(ldpm_t h, void *buf);
+int ldpm_load_checkpoint(ldpm_t h, const void *buf);
+
+/* Release everything the handle owns (synchronises first).  NULL is a no-op. */
+void ldpm_destroy(ldpm_t h);
+
+/* Message of the last failing call on this thread ("" if none).  Valid until the next call. */
+const char *ldpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPM_H */

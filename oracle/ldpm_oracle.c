@@ -27,11 +27,15 @@
  *   - e_max is updated only in the fracture branch; omega is evaluated at the current strain;
  *   - e_N > 0 selects the fracture branch, e_N <= 0 the compression/friction branch;
  *   - e_V of a tetrahedron is its linearised volumetric strain Delta V / (3 V0) = (1/3) div u;
+ *   - in the fracture branch an effective strain below 1e-150 (where t/e is 0/0 in floating point)
+ *     takes the elastic limit t = E e;
  *   - k_t > 0 (tensile reloading), E_d != E0 and r_s != 0 are outside what is pinned here.
  */
 #include <math.h>
 
 #define ORC_PI 3.14159265358979323846
+/* effective strains below this are treated as zero in the fracture law (squares would underflow) */
+#define ORC_TINY_STRAIN 1e-150
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -108,6 +112,15 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
         /* App. A.1, fracture.  Effective strain e = sqrt(e_N^2 + alpha (e_M^2 + e_L^2)). */
         double eT2 = e[1] * e[1] + e[2] * e[2];
         double eeff = sqrt(e[0] * e[0] + alpha * eT2);
+        if (eeff < ORC_TINY_STRAIN) {
+            /* The ratio t / e of the expressions below is 0/0 at e = 0; its limit on the elastic
+             * path is E0, so a vanishing effective strain responds elastically, t = E e. */
+            t_new[0] = E0 * e[0];
+            t_new[1] = alpha * E0 * e[1];
+            t_new[2] = alpha * E0 * e[2];
+            *emax_new = emax_old > eeff ? emax_old : eeff;
+            return;
+        }
         /* Coupling angle, tan(omega) = e_N / sqrt(alpha (e_M^2 + e_L^2)). */
         double omega = atan2(e[0], sqrt(alpha * eT2));
         double s = sin(omega), c = cos(omega);

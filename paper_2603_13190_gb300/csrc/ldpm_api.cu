@@ -1,0 +1,1204 @@
+// ldpm_api.cu -- host runtime behind the C ABI of include/ldpm.h.
+//
+// Set-up (ldpm_create): validation of the mesh rules, facet frames/arms/projected areas
+// (paper Sec. 2), lumped mass (Sec. 3.2.5), Morton ordering of particles and tetrahedra, the
+// particle-to-facet-end CSR list in a fixed order, upload, and the critical-step estimate.
+// Stepping (ldpm_step): the kernels of ldpm_kernels.cu, replayed from captured CUDA graphs.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <numeric>
+#include <random>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ldpm.h"
+#include "ldpm_internal.h"
+
+using namespace ldpm;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                                    \
+    do {                                                                                            \
+        cudaError_t e_ = (call);                                                                    \
+        if (e_ != cudaSuccess)                                                                      \
+            return fail(e_ == cudaErrorMemoryAllocation ? LDPM_E_OOM : LDPM_E_CUDA, "%s: %s (%s:%d)", \
+                        #call, cudaGetErrorString(e_), __FILE__, __LINE__);                         \
+    } while (0)
+
+constexpr int kTile = 32;  // tetrahedra per facet-pass block (padding granularity)
+constexpr int kEdgeA[6] = {0, 0, 0, 1, 1, 2};
+constexpr int kEdgeB[6] = {1, 2, 3, 2, 3, 3};
+
+int edge_of(int a, int b)
+{
+    if (a > b) std::swap(a, b);
+    for (int e = 0; e < 6; ++e)
+        if (kEdgeA[e] == a && kEdgeB[e] == b) return e;
+    return -1;
+}
+
+uint32_t spread10(uint32_t v)
+{
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000ffu;
+    v = (v | (v << 8)) & 0x0300f00fu;
+    v = (v | (v << 4)) & 0x030c30c3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+uint32_t morton3(const double *p, const double *lo, const double *span)
+{
+    uint32_t c[3];
+    for (int a = 0; a < 3; ++a) {
+        double t = span[a] > 0 ? (p[a] - lo[a]) / span[a] : 0.0;
+        t = std::min(std::max(t, 0.0), 1.0);
+        c[a] = (uint32_t)std::min(1023.0, std::floor(t * 1024.0));
+    }
+    return spread10(c[0]) | (spread10(c[1]) << 1) | (spread10(c[2]) << 2);
+}
+
+template <class R>
+void law_const(const ldpm_material &mt, double dt, LawConst<R> &c)
+{
+    const double E0 = mt.E0, a = mt.alpha;
+    c.E0 = R(E0);
+    c.alpha = R(a);
+    c.inv_alpha = R(1.0 / a);
+    c.sigma_t = R(mt.sigma_t);
+    c.four_alpha_over_r2 = R(4.0 * a / (mt.r_st * mt.r_st));
+    c.Hs_over_alpha = R(mt.r_s * E0 / a);
+    c.n_t = R(mt.n_t);
+    c.l_t = R(mt.l_t);
+    c.sigma_c0 = R(mt.sigma_c0);
+    c.Hc0 = R(mt.Hc0_E0 * E0);
+    c.Hc1 = R(mt.Hc1_E0 * E0);
+    c.kc1 = R(mt.kc1);
+    c.kc2 = R(mt.kc2);
+    c.ec0 = R(mt.sigma_c0 / E0);
+    c.ec1 = R(mt.kc0 * mt.sigma_c0 / E0);
+    c.eV0 = R(mt.kc3 * mt.sigma_c0 / E0);
+    c.beta = R(mt.beta);
+    c.Ed = R(mt.Ed_E0 * E0);
+    c.mu_diff_sN0 = R((mt.mu0 - mt.mu_inf) * mt.sigma_N0);
+    c.mu_inf = R(mt.mu_inf);
+    c.inv_sigma_N0 = R(1.0 / mt.sigma_N0);
+    c.sigma_s = R(mt.r_st * mt.sigma_t);
+    c.dt = R(dt);
+    // FP32: squares of strains below ~1e-19 underflow; 1e-15 keeps every product of the law normal
+    // and changes tractions by < E0 * 1e-15.  FP64: the oracle's threshold.
+    c.tiny_strain = R(sizeof(R) == 4 ? 1e-15 : 1e-150);
+    c.elastic = mt.elastic;
+}
+
+struct SpecHost {
+    int32_t N = 0, T = 0, F = 0;  // caller sizes
+    int32_t p0 = 0, t0 = 0;        // internal offsets (t0 multiple of kTile)
+    int32_t T_pad = 0;
+    ldpm_material mat{};
+    double dt = 0, ramp_time = 0, W_kin0 = 0;
+    std::vector<int32_t> perm_p;  // internal rank -> caller particle
+    std::vector<int32_t> inv_p;   // caller particle -> internal rank
+    std::vector<int64_t> fmap;    // caller facet -> internal facet (global index)
+    std::vector<uint8_t> fswap;   // caller facet I is the internal b vertex
+};
+
+}  // namespace
+
+struct ldpm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int prec = LDPM_FP64;
+    int graph_chunk = 32;
+    DeviceModel dm;
+    std::vector<SpecHost> sp;
+    std::vector<double> x_int;     // [N][3] internal order
+    std::vector<double> inv_mass;  // [N][6]
+    std::vector<double> pconst_h;  // [N][8]
+    double *d_partial = nullptr, *d_out16 = nullptr, *h_out16 = nullptr;
+    std::map<int64_t, cudaGraphExec_t> graphs;
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_pairs;  // (kernel id, event index of start)
+    double prof_ms[3] = {0, 0, 0};
+    int64_t prof_cnt[3] = {0, 0, 0};
+    size_t rsize() const { return prec == LDPM_MIXED ? sizeof(float) : sizeof(double); }
+    size_t r4size() const { return 4 * rsize(); }
+};
+
+namespace {
+
+void free_model(ldpm_ctx *h)
+{
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.bc_vel, h->dm.f_ext, h->dm.tet, h->dm.geo,
+                    h->dm.hist, h->dm.fout, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
+                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->h_out16) cudaFreeHost(h->h_out16);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+template <class T>
+int dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return fail(e == cudaErrorMemoryAllocation ? LDPM_E_OOM : LDPM_E_CUDA, "cudaMalloc of %zu bytes: %s",
+                    count * sizeof(T), cudaGetErrorString(e));
+    }
+    return LDPM_OK;
+}
+
+int check_material(const ldpm_material &m)
+{
+    const double v[] = {m.rho, m.E0, m.alpha, m.sigma_t, m.l_t, m.r_st, m.n_t, m.sigma_c0, m.Hc0_E0, m.Hc1_E0,
+                        m.kc0, m.kc1, m.kc2, m.kc3, m.mu0, m.mu_inf, m.sigma_N0, m.Ed_E0, m.beta, m.k_t, m.r_s};
+    for (double x : v)
+        if (!std::isfinite(x)) return fail(LDPM_E_INVALID_ARG, "material parameter is not finite");
+    if (!(m.rho > 0 && m.E0 > 0 && m.alpha > 0 && m.sigma_t > 0 && m.l_t > 0 && m.r_st > 0 && m.n_t >= 0 &&
+          m.sigma_c0 > 0 && m.kc0 >= 1 && m.kc3 > 0 && m.sigma_N0 > 0))
+        return fail(LDPM_E_INVALID_ARG, "material: rho, E0, alpha, sigma_t, l_t, r_st, sigma_c0, kc3, sigma_N0 "
+                                        "must be > 0, n_t >= 0, kc0 >= 1");
+    if (m.k_t != 0.0) return fail(LDPM_E_UNSUPPORTED, "k_t != 0 (tensile reloading) is not implemented");
+    if (m.r_s != 0.0) return fail(LDPM_E_UNSUPPORTED, "r_s != 0 (shear cohesion softening) is not implemented");
+    if (m.Ed_E0 != 1.0) return fail(LDPM_E_UNSUPPORTED, "Ed_E0 != 1 is not implemented");
+    if (m.reserved != 0) return fail(LDPM_E_INVALID_ARG, "material.reserved must be 0");
+    return LDPM_OK;
+}
+
+// Per-specimen host preprocessing into the internal layout.  Writes this specimen's slices of the
+// host mirrors of every device array.
+struct HostArrays {
+    std::vector<double> pstate, pdyn, pconst, bc_vel, f_ext;
+    std::vector<int4> tet;
+    std::vector<double> geo64;  // [Fint][4] before rounding to R
+    std::vector<int32_t> row;
+    std::vector<double> ent64;  // [2 Fint][3] arms
+    std::vector<int64_t> ent_id;
+    std::vector<int32_t> tile_spec;
+    bool any_fext = false;
+};
+
+int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecHost &S, HostArrays &H,
+                     std::vector<double> &x_int, std::vector<double> &inv_mass, std::vector<double> &pconst_h)
+{
+    const int32_t N = g.n_particles, T = g.n_tets, F = g.n_facets;
+    if (N < 4 || T < 1 || F != 12 * T)
+        return fail(LDPM_E_BAD_GEOMETRY, "specimen %d: need N >= 4, T >= 1 and F == 12 T (N=%d T=%d F=%d)", s, N,
+                    T, F);
+    if (!g.x || !g.tet || !g.facet_pi || !g.facet_pj || !g.facet_tet || !g.facet_vtx)
+        return fail(LDPM_E_INVALID_ARG, "specimen %d: geometry array is NULL", s);
+    if (!g.diameter && !g.inertia)
+        return fail(LDPM_E_INVALID_ARG, "specimen %d: need diameter or inertia", s);
+    const ldpm_material &mat = S.mat;
+    // ---- tetrahedra
+    std::vector<double> tvol(T);
+    for (int32_t t = 0; t < T; ++t) {
+        const int32_t *v = g.tet + 4 * (size_t)t;
+        for (int i = 0; i < 4; ++i) {
+            if (v[i] < 0 || v[i] >= N) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: particle index out of range", t);
+            for (int k = 0; k < i; ++k)
+                if (v[k] == v[i]) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: repeated particle", t);
+        }
+        double d[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int a = 0; a < 3; ++a) d[i][a] = g.x[3 * (size_t)v[i + 1] + a] - g.x[3 * (size_t)v[0] + a];
+        const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
+                           d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
+                           d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
+        if (!(std::fabs(det) > 0) || !std::isfinite(det))
+            return fail(LDPM_E_BAD_GEOMETRY, "tet %d: zero or non-finite volume", t);
+        tvol[t] = std::fabs(det) / 6.0;
+    }
+    for (int32_t i = 0; i < 3 * N; ++i)
+        if (!std::isfinite(g.x[i])) return fail(LDPM_E_BAD_GEOMETRY, "particle coordinate is not finite");
+    // ---- Morton order of particles and tetrahedra
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY}, span[3];
+    for (int32_t i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = std::min(lo[a], g.x[3 * (size_t)i + a]);
+            hi[a] = std::max(hi[a], g.x[3 * (size_t)i + a]);
+        }
+    for (int a = 0; a < 3; ++a) span[a] = hi[a] - lo[a];
+    std::vector<uint32_t> key(N);
+    for (int32_t i = 0; i < N; ++i) key[i] = morton3(g.x + 3 * (size_t)i, lo, span);
+    S.perm_p.resize(N);
+    std::iota(S.perm_p.begin(), S.perm_p.end(), 0);
+    std::stable_sort(S.perm_p.begin(), S.perm_p.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    S.inv_p.assign(N, 0);
+    for (int32_t r = 0; r < N; ++r) S.inv_p[S.perm_p[r]] = r;
+    std::vector<uint32_t> tkey(T);
+    for (int32_t t = 0; t < T; ++t) {
+        double c[3] = {0, 0, 0};
+        for (int i = 0; i < 4; ++i)
+            for (int a = 0; a < 3; ++a) c[a] += 0.25 * g.x[3 * (size_t)g.tet[4 * (size_t)t + i] + a];
+        tkey[t] = morton3(c, lo, span);
+    }
+    std::vector<int32_t> perm_t(T), inv_t(T);
+    std::iota(perm_t.begin(), perm_t.end(), 0);
+    std::stable_sort(perm_t.begin(), perm_t.end(), [&](int32_t a, int32_t b) { return tkey[a] < tkey[b]; });
+    for (int32_t r = 0; r < T; ++r) inv_t[perm_t[r]] = r;
+
+    // ---- particles: positions, lumped mass (Sec. 3.2.5), BCs, initial velocity
+    std::vector<double> mass(N, 0.0);
+    for (int32_t t = 0; t < T; ++t)
+        for (int i = 0; i < 4; ++i) mass[g.tet[4 * (size_t)t + i]] += mat.rho * tvol[t] / 4.0;
+    double dpos = INFINITY;
+    if (g.diameter)
+        for (int32_t i = 0; i < N; ++i)
+            if (g.diameter[i] > 0 && g.diameter[i] < dpos) dpos = g.diameter[i];
+    S.W_kin0 = 0.0;
+    for (int32_t i = 0; i < N; ++i) {
+        const int32_t r = S.inv_p[i];
+        const size_t P = (size_t)S.p0 + r;
+        const double mi = g.mass ? g.mass[i] : mass[i];
+        double md[6];
+        for (int a = 0; a < 3; ++a) {
+            md[a] = mi;
+            if (g.inertia) {
+                md[3 + a] = g.inertia[3 * (size_t)i + a];
+            } else {
+                const double d = g.diameter[i] > 0 ? g.diameter[i] : dpos;
+                md[3 + a] = mi * d * d / 10.0;
+            }
+        }
+        uint64_t bits = 0;
+        for (int k = 0; k < 6; ++k) {
+            if (!(md[k] > 0) || !std::isfinite(md[k]))
+                return fail(LDPM_E_BAD_GEOMETRY, "particle %d: non-positive mass or inertia", i);
+            const int mk = o.bc_mask ? o.bc_mask[6 * (size_t)i + k] : 0;
+            if (mk < 0 || mk > 2) return fail(LDPM_E_INVALID_ARG, "bc_mask must be 0, 1 or 2");
+            bits |= (uint64_t)mk << (8 * k);
+            inv_mass[6 * P + k] = 1.0 / md[k];
+            pconst_h[8 * P + k] = 1.0 / md[k];
+            const double vb = o.bc_vel ? o.bc_vel[6 * (size_t)i + k] : 0.0;
+            H.bc_vel[6 * P + k] = vb;
+            if (o.f_ext) {
+                H.f_ext[6 * P + k] = o.f_ext[6 * (size_t)i + k];
+                H.any_fext = true;
+            }
+            double v = o.v0 ? o.v0[6 * (size_t)i + k] : 0.0;
+            if (mk == 1) v = 0.0;
+            if (mk == 2) v = vb * (o.ramp_time <= 0 ? 1.0 : 0.0);
+            H.pstate[16 * P + 9 + k] = v;
+            S.W_kin0 += 0.5 * md[k] * v * v;
+        }
+        int64_t sb;
+        std::memcpy(&pconst_h[8 * P + 6], &bits, 8);
+        sb = s;
+        std::memcpy(&pconst_h[8 * P + 7], &sb, 8);
+        for (int a = 0; a < 3; ++a) {
+            H.pstate[16 * P + a] = g.x[3 * (size_t)i + a];
+            x_int[3 * P + a] = g.x[3 * (size_t)i + a];
+        }
+    }
+    // ---- tetrahedra in Morton order (padding tetrahedra keep particle id -1)
+    for (int32_t r = 0; r < T; ++r) {
+        const int32_t *v = g.tet + 4 * (size_t)perm_t[r];
+        H.tet[(size_t)S.t0 + r] = make_int4(S.p0 + S.inv_p[v[0]], S.p0 + S.inv_p[v[1]], S.p0 + S.inv_p[v[2]],
+                                            S.p0 + S.inv_p[v[3]]);
+    }
+    for (int32_t r = 0; r < S.T_pad / kTile; ++r) H.tile_spec[S.t0 / kTile + r] = s;
+    // ---- facets: slot = 2 * edge + k within the tetrahedron
+    S.fmap.assign(F, -1);
+    S.fswap.assign(F, 0);
+    std::vector<uint8_t> used((size_t)T * 12, 0);
+    for (int32_t k = 0; k < F; ++k) {
+        const int32_t t = g.facet_tet[k];
+        if (t < 0 || t >= T) return fail(LDPM_E_BAD_GEOMETRY, "facet %d: tetrahedron index out of range", k);
+        const int32_t *v = g.tet + 4 * (size_t)t;
+        int la = -1, lb = -1;
+        for (int i = 0; i < 4; ++i) {
+            if (v[i] == g.facet_pi[k]) la = i;
+            if (v[i] == g.facet_pj[k]) lb = i;
+        }
+        if (la < 0 || lb < 0 || la == lb)
+            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: I and J must be two vertices of its tetrahedron", k);
+        const int e = edge_of(la, lb);
+        const int32_t rt = inv_t[t];
+        int slot = 2 * e;
+        if (used[(size_t)rt * 12 + slot]) ++slot;
+        if (used[(size_t)rt * 12 + slot])
+            return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: more than 2 facets on one edge", t);
+        used[(size_t)rt * 12 + slot] = 1;
+        const int64_t fi = ((int64_t)S.t0 + rt) * 12 + slot;
+        S.fmap[k] = fi;
+        S.fswap[k] = la > lb;
+        // geometry from the internal first vertex a = min(la, lb)
+        const int32_t pa = v[std::min(la, lb)], pb = v[std::max(la, lb)];
+        const double *xa = g.x + 3 * (size_t)pa, *xb = g.x + 3 * (size_t)pb;
+        const double *p0 = g.facet_vtx + 9 * (size_t)k;
+        double dd[3], e1[3], e2[3], xc[3];
+        for (int a = 0; a < 3; ++a) {
+            dd[a] = xb[a] - xa[a];
+            e1[a] = p0[3 + a] - p0[a];
+            e2[a] = p0[6 + a] - p0[a];
+            xc[a] = (p0[a] + p0[3 + a] + p0[6 + a]) / 3.0;
+        }
+        const double l = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double nc[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                              e1[0] * e2[1] - e1[1] * e2[0]};
+        const double twoA0 = std::sqrt(nc[0] * nc[0] + nc[1] * nc[1] + nc[2] * nc[2]);
+        if (!(l > 0) || !(twoA0 > 0) || !std::isfinite(twoA0))
+            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: zero edge length or facet area", k);
+        if (!(l < mat.l_t))
+            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: edge length %g >= l_t (softening modulus undefined)", k, l);
+        // projected area A = A0 |n . n0| (Sec. 2)
+        const double A = 0.5 * std::fabs((dd[0] * nc[0] + dd[1] * nc[1] + dd[2] * nc[2]) / l);
+        for (int a = 0; a < 3; ++a) {
+            H.geo64[4 * (size_t)fi + a] = xc[a] - xa[a];
+            H.ent64[6 * (size_t)fi + a] = xc[a] - xa[a];      // arm of side 0 (vertex a)
+            H.ent64[6 * (size_t)fi + 3 + a] = xc[a] - xb[a];  // arm of side 1 (vertex b)
+        }
+        H.geo64[4 * (size_t)fi + 3] = A;
+    }
+    for (int32_t r = 0; r < T; ++r)
+        for (int sl = 0; sl < 12; ++sl)
+            if (!used[(size_t)r * 12 + sl])
+                return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: edge without its two facets", perm_t[r]);
+    return LDPM_OK;
+}
+
+template <class R>
+int upload_facets(ldpm_ctx *h, const HostArrays &H, int64_t Fint)
+{
+    using T4 = R4<R>;
+    std::vector<T4> geo(Fint), ent(2 * Fint);
+    for (int64_t f = 0; f < Fint; ++f) {
+        geo[f].x = R(H.geo64[4 * f]);
+        geo[f].y = R(H.geo64[4 * f + 1]);
+        geo[f].z = R(H.geo64[4 * f + 2]);
+        geo[f].w = R(H.geo64[4 * f + 3]);
+    }
+    const int64_t nent = H.ent_id.size();
+    for (int64_t r = 0; r < nent; ++r) {
+        const int64_t id = H.ent_id[r];  // facet << 1 | side
+        const int64_t f = id >> 1, side = id & 1;
+        ent[r].x = R(H.ent64[6 * f + 3 * side]);
+        ent[r].y = R(H.ent64[6 * f + 3 * side + 1]);
+        ent[r].z = R(H.ent64[6 * f + 3 * side + 2]);
+        if (sizeof(R) == 4) {
+            const int32_t b = (int32_t)id;
+            std::memcpy(&ent[r].w, &b, 4);
+        } else {
+            std::memcpy(&ent[r].w, &id, 8);
+        }
+    }
+    int rc;
+    if ((rc = dalloc((T4 **)&h->dm.geo, Fint)) || (rc = dalloc((T4 **)&h->dm.hist, Fint)) ||
+        (rc = dalloc((T4 **)&h->dm.fout, Fint)) || (rc = dalloc((T4 **)&h->dm.ent, std::max<int64_t>(nent, 1))))
+        return rc;
+    CU(cudaMemcpy(h->dm.geo, geo.data(), Fint * sizeof(T4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.ent, ent.data(), nent * sizeof(T4), cudaMemcpyHostToDevice));
+    CU(cudaMemset(h->dm.hist, 0, Fint * sizeof(T4)));
+    CU(cudaMemset(h->dm.fout, 0, Fint * sizeof(T4)));
+    std::vector<LawConst<R>> law(h->sp.size());
+    for (size_t s = 0; s < h->sp.size(); ++s) law_const<R>(h->sp[s].mat, h->sp[s].dt, law[s]);
+    if ((rc = dalloc((LawConst<R> **)&h->dm.law, law.size()))) return rc;
+    CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(LawConst<R>), cudaMemcpyHostToDevice));
+    return LDPM_OK;
+}
+
+int update_law(ldpm_ctx *h)
+{
+    if (h->prec == LDPM_MIXED) {
+        std::vector<LawConst<float>> law(h->sp.size());
+        for (size_t s = 0; s < h->sp.size(); ++s) law_const<float>(h->sp[s].mat, h->sp[s].dt, law[s]);
+        CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(law[0]), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<LawConst<double>> law(h->sp.size());
+        for (size_t s = 0; s < h->sp.size(); ++s) law_const<double>(h->sp[s].mat, h->sp[s].dt, law[s]);
+        CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(law[0]), cudaMemcpyHostToDevice));
+    }
+    std::vector<SpecDyn> sd(h->sp.size());
+    for (size_t s = 0; s < h->sp.size(); ++s) sd[s] = SpecDyn{h->sp[s].dt, h->sp[s].ramp_time};
+    CU(cudaMemcpy(h->dm.spec, sd.data(), sd.size() * sizeof(SpecDyn), cudaMemcpyHostToDevice));
+    return LDPM_OK;
+}
+
+int launch_facet_any(ldpm_ctx *h, int mode, const double *pst)
+{
+    cudaError_t e = h->prec == LDPM_MIXED ? launch_facet<float>(h->dm, mode, pst, h->stream)
+                                          : launch_facet<double>(h->dm, mode, pst, h->stream);
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "facet pass launch: %s", cudaGetErrorString(e));
+    return LDPM_OK;
+}
+
+int launch_gather_any(ldpm_ctx *h, int mode, double *out6)
+{
+    cudaError_t e = h->prec == LDPM_MIXED ? launch_gather<float>(h->dm, mode, out6, h->stream)
+                                          : launch_gather<double>(h->dm, mode, out6, h->stream);
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "particle pass launch: %s", cudaGetErrorString(e));
+    return LDPM_OK;
+}
+
+// Rebuild the node force sums of the current state from the stored tractions (f = sum A P t).
+int forces_from_history(ldpm_ctx *h)
+{
+    int rc;
+    double *out6 = nullptr;
+    if ((rc = dalloc(&out6, 6 * (size_t)h->dm.N))) return rc;
+    if ((rc = launch_facet_any(h, FACET_FROM_HIST, nullptr)) || (rc = launch_gather_any(h, GATHER_ASSEMBLE, out6))) {
+        cudaFree(out6);
+        return rc;
+    }
+    cudaError_t e = cudaMemcpy2DAsync(h->dm.pdyn, 8 * sizeof(double), out6, 6 * sizeof(double), 6 * sizeof(double),
+                                      h->dm.N, cudaMemcpyDeviceToDevice, h->stream);
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaFree(out6);
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(LDPM_E_CUDA, "force rebuild: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return LDPM_OK;
+}
+
+// Largest eigenvalue of M^-1 K per specimen by power iteration; the elastic operator is one facet
+// pass (t = E e at displacement x) plus one assembly.  Host-side vector algebra, device mat-vec.
+int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
+{
+    const int32_t N = h->dm.N;
+    const size_t n6 = 6 * (size_t)N;
+    int rc;
+    double *pst = nullptr, *out6 = nullptr;
+    if ((rc = dalloc(&pst, 16 * (size_t)N)) || (rc = dalloc(&out6, n6))) {
+        cudaFree(pst);
+        return rc;
+    }
+    std::vector<double> ps(16 * (size_t)N, 0.0), x(n6), f(n6);
+    for (int32_t p = 0; p < N; ++p)
+        for (int a = 0; a < 3; ++a) ps[16 * (size_t)p + a] = h->x_int[3 * (size_t)p + a];
+    std::mt19937_64 rng(12345);
+    std::normal_distribution<double> nd;
+    for (auto &v : x) v = nd(rng);
+    const int nsp = (int)h->sp.size();
+    lam.assign(nsp, 0.0);
+    std::vector<double> prev(nsp, 0.0);
+    const int max_it = 400;
+    for (int it = 0; it < max_it; ++it) {
+        for (int s = 0; s < nsp; ++s) {
+            const size_t a = 6 * (size_t)h->sp[s].p0, b = a + 6 * (size_t)h->sp[s].N;
+            double nrm = 0;
+            for (size_t i = a; i < b; ++i) nrm += x[i] * x[i] / h->inv_mass[i];
+            nrm = std::sqrt(nrm);
+            for (size_t i = a; i < b; ++i) x[i] /= nrm;
+        }
+        for (int32_t p = 0; p < N; ++p)
+            for (int k = 0; k < 6; ++k) ps[16 * (size_t)p + 3 + k] = x[6 * (size_t)p + k];
+        CU(cudaMemcpyAsync(pst, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        if ((rc = launch_facet_any(h, FACET_ELASTIC, pst)) || (rc = launch_gather_any(h, GATHER_ASSEMBLE, out6))) break;
+        CU(cudaMemcpyAsync(f.data(), out6, n6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        bool done = it >= 30;
+        for (int s = 0; s < nsp; ++s) {
+            const size_t a = 6 * (size_t)h->sp[s].p0, b = a + 6 * (size_t)h->sp[s].N;
+            double xkx = 0;
+            for (size_t i = a; i < b; ++i) xkx -= x[i] * f[i];
+            lam[s] = xkx;  // x^T M x = 1
+            if (std::fabs(lam[s] - prev[s]) > 1e-5 * std::fabs(lam[s])) done = false;
+            prev[s] = lam[s];
+        }
+        for (size_t i = 0; i < n6; ++i) x[i] = -f[i] * h->inv_mass[i];
+        if (done) break;
+    }
+    cudaFree(pst);
+    cudaFree(out6);
+    if (rc) return rc;
+    for (int s = 0; s < nsp; ++s)
+        if (!(lam[s] > 0) || !std::isfinite(lam[s]))
+            return fail(LDPM_E_BAD_GEOMETRY, "specimen %d: critical step estimate failed (lambda %g)", s, lam[s]);
+    return LDPM_OK;
+}
+
+int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, const ldpm_options *opts,
+                 ldpm_t *out)
+{
+    if (!out) return fail(LDPM_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || !geoms || !mats || !opts) return fail(LDPM_E_INVALID_ARG, "need n >= 1 and non-NULL arrays");
+    const ldpm_options &o0 = opts[0];
+    if (o0.precision != LDPM_FP64 && o0.precision != LDPM_MIXED)
+        return fail(LDPM_E_INVALID_ARG, "precision must be LDPM_FP64 or LDPM_MIXED");
+    for (int s = 0; s < n; ++s) {
+        if (opts[s].precision != o0.precision) return fail(LDPM_E_INVALID_ARG, "specimens must share the precision");
+        if (opts[s].reserved != 0) return fail(LDPM_E_INVALID_ARG, "options.reserved must be 0");
+        if (!std::isfinite(opts[s].dt) || !std::isfinite(opts[s].ramp_time))
+            return fail(LDPM_E_INVALID_ARG, "dt and ramp_time must be finite");
+        int rc = check_material(mats[s]);
+        if (rc) return rc;
+    }
+    std::unique_ptr<ldpm_ctx> h(new (std::nothrow) ldpm_ctx);
+    if (!h) return fail(LDPM_E_OOM, "host allocation");
+    h->prec = o0.precision;
+    h->graph_chunk = o0.graph_chunk == 0 ? 32 : o0.graph_chunk;
+    h->sp.resize(n);
+    int64_t Np = 0, Tp = 0;
+    for (int s = 0; s < n; ++s) {
+        SpecHost &S = h->sp[s];
+        S.N = geoms[s].n_particles;
+        S.T = geoms[s].n_tets;
+        S.F = geoms[s].n_facets;
+        if (S.N < 4 || S.T < 1 || (int64_t)S.F != 12 * (int64_t)S.T)
+            return fail(LDPM_E_BAD_GEOMETRY, "specimen %d: need N >= 4, T >= 1 and F == 12 T", s);
+        S.mat = mats[s];
+        S.ramp_time = opts[s].ramp_time;
+        S.dt = opts[s].dt;
+        S.p0 = (int32_t)Np;
+        S.t0 = (int32_t)Tp;
+        S.T_pad = (S.T + kTile - 1) / kTile * kTile;
+        Np += S.N;
+        Tp += S.T_pad;
+    }
+    if (Np > INT32_MAX / 2 || 24 * Tp > (int64_t)1 << 30)
+        return fail(LDPM_E_INVALID_ARG, "specimen too large for 32-bit facet-end ids");
+    const int32_t N = (int32_t)Np, T = (int32_t)Tp;
+    const int64_t Fint = 12 * (int64_t)T;
+    HostArrays H;
+    H.pstate.assign(16 * (size_t)N, 0.0);
+    H.pdyn.assign(8 * (size_t)N, 0.0);
+    H.bc_vel.assign(6 * (size_t)N, 0.0);
+    H.f_ext.assign(6 * (size_t)N, 0.0);
+    H.tet.assign(T, make_int4(-1, -1, -1, -1));
+    H.geo64.assign(4 * (size_t)Fint, 0.0);
+    H.ent64.assign(6 * (size_t)Fint, 0.0);
+    H.tile_spec.assign(T / kTile, 0);
+    h->x_int.assign(3 * (size_t)N, 0.0);
+    h->inv_mass.assign(6 * (size_t)N, 0.0);
+    h->pconst_h.assign(8 * (size_t)N, 0.0);
+    for (int s = 0; s < n; ++s) {
+        int rc = prepare_specimen(s, geoms[s], opts[s], h->sp[s], H, h->x_int, h->inv_mass, h->pconst_h);
+        if (rc) return rc;
+    }
+    // ---- CSR of facet ends, ascending facet id within each particle (fixed summation order)
+    H.row.assign((size_t)N + 1, 0);
+    for (int64_t t = 0; t < T; ++t) {
+        const int4 v = H.tet[t];
+        if (v.x < 0) continue;
+        const int vv[4] = {v.x, v.y, v.z, v.w};
+        for (int sl = 0; sl < 12; ++sl) {
+            const int e = sl >> 1;
+            H.row[vv[kEdgeA[e]] + 1]++;
+            H.row[vv[kEdgeB[e]] + 1]++;
+        }
+    }
+    for (int32_t p = 0; p < N; ++p) H.row[p + 1] += H.row[p];
+    H.ent_id.assign(H.row[N], 0);
+    {
+        std::vector<int32_t> pos(H.row.begin(), H.row.end() - 1);
+        for (int64_t t = 0; t < T; ++t) {
+            const int4 v = H.tet[t];
+            if (v.x < 0) continue;
+            const int vv[4] = {v.x, v.y, v.z, v.w};
+            for (int sl = 0; sl < 12; ++sl) {
+                const int e = sl >> 1;
+                const int64_t f = 12 * t + sl;
+                H.ent_id[pos[vv[kEdgeA[e]]]++] = (f << 1) | 0;
+                H.ent_id[pos[vv[kEdgeB[e]]]++] = (f << 1) | 1;
+            }
+        }
+    }
+    // ---- device
+    int dev = o0.device;
+    if (dev < 0) CU(cudaGetDevice(&dev));
+    CU(cudaSetDevice(dev));
+    h->device = dev;
+    if (o0.cuda_stream) {
+        h->stream = (cudaStream_t)o0.cuda_stream;
+    } else {
+        CU(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+        h->own_stream = true;
+    }
+    ldpm_ctx *raw = h.get();
+    struct Guard {
+        ldpm_ctx *p;
+        bool armed = true;
+        ~Guard()
+        {
+            if (armed) free_model(p);
+        }
+    } guard{raw};
+    DeviceModel &dm = h->dm;
+    dm.N = N;
+    dm.T = T;
+    dm.n_spec = n;
+    dm.tets_per_block = kTile;
+    int rc;
+    if ((rc = dalloc(&dm.pstate, 16 * (size_t)N)) || (rc = dalloc(&dm.pdyn, 8 * (size_t)N)) ||
+        (rc = dalloc(&dm.pconst, 8 * (size_t)N)) || (rc = dalloc(&dm.bc_vel, 6 * (size_t)N)) ||
+        (rc = dalloc(&dm.tet, (size_t)T)) || (rc = dalloc(&dm.row, (size_t)N + 1)) ||
+        (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
+        (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
+        (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))))
+        return rc;
+    if (H.any_fext) {
+        if ((rc = dalloc(&dm.f_ext, 6 * (size_t)N))) return rc;
+        CU(cudaMemcpy(dm.f_ext, H.f_ext.data(), H.f_ext.size() * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    CU(cudaMallocHost((void **)&h->h_out16, 16 * sizeof(double)));
+    CU(cudaMemcpy(dm.pstate, H.pstate.data(), H.pstate.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.pdyn, H.pdyn.data(), H.pdyn.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.pconst, h->pconst_h.data(), h->pconst_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.bc_vel, H.bc_vel.data(), H.bc_vel.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.tet, H.tet.data(), H.tet.size() * sizeof(int4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.row, H.row.data(), H.row.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.tile_spec, H.tile_spec.data(), H.tile_spec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CU(cudaMemset(dm.step, 0, sizeof(int64_t)));
+    CU(cudaMemset(dm.flag, 0, sizeof(int32_t)));
+    for (auto &S : h->sp)
+        if (!(S.dt > 0)) S.dt = 1.0;  // placeholder until estimated
+    if (h->prec == LDPM_MIXED)
+        rc = upload_facets<float>(raw, H, Fint);
+    else
+        rc = upload_facets<double>(raw, H, Fint);
+    if (rc) return rc;
+    if ((rc = update_law(raw))) return rc;
+    // ---- time step: given, or dt_factor * 2 / sqrt(lambda_max)
+    bool need = false;
+    for (int s = 0; s < n; ++s) need |= !(opts[s].dt > 0);
+    if (need) {
+        std::vector<double> lam;
+        if ((rc = estimate_dt(raw, lam))) return rc;
+        for (int s = 0; s < n; ++s)
+            if (!(opts[s].dt > 0)) {
+                const double fac = opts[s].dt_factor > 0 ? opts[s].dt_factor : 0.9;
+                h->sp[s].dt = fac * 2.0 / std::sqrt(lam[s]);
+            }
+        if ((rc = update_law(raw))) return rc;
+        CU(cudaMemset(dm.fout, 0, Fint * h->r4size()));
+    }
+    CU(cudaDeviceSynchronize());
+    guard.armed = false;
+    *out = h.release();
+    return LDPM_OK;
+}
+
+int enqueue_direct(ldpm_ctx *h, int64_t nsteps, bool with_kick, bool last)
+{
+    int rc;
+    if (with_kick) {
+        cudaError_t e = launch_kick(h->dm, h->stream);
+        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "kick launch: %s", cudaGetErrorString(e));
+    }
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const bool lst = last && i == nsteps - 1;
+        if ((rc = launch_facet_any(h, FACET_STEP, nullptr))) return rc;
+        if ((rc = launch_gather_any(h, lst ? GATHER_STEP_LAST : GATHER_STEP_MID, nullptr))) return rc;
+    }
+    return LDPM_OK;
+}
+
+int graph_for(ldpm_ctx *h, int64_t len, cudaGraphExec_t *exec)
+{
+    auto it = h->graphs.find(len);
+    if (it != h->graphs.end()) {
+        *exec = it->second;
+        return LDPM_OK;
+    }
+    cudaGraph_t g = nullptr;
+    CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = enqueue_direct(h, len, false, false);
+    cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    if (rc) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "graph capture: %s", cudaGetErrorString(e));
+    cudaGraphExec_t ex = nullptr;
+    e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "graph instantiate: %s", cudaGetErrorString(e));
+    h->graphs[len] = ex;
+    *exec = ex;
+    return LDPM_OK;
+}
+
+int enqueue_profiled(ldpm_ctx *h, int64_t nsteps)
+{
+    auto rec = [&](int kid, auto &&launch) -> int {
+        cudaEvent_t a, b;
+        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+            return fail(LDPM_E_CUDA, "event create failed");
+        h->ev_pool.push_back(a);
+        h->ev_pool.push_back(b);
+        h->ev_pairs.push_back({kid, (int)h->ev_pool.size() - 2});
+        CU(cudaEventRecord(a, h->stream));
+        int rc = launch();
+        if (rc) return rc;
+        CU(cudaEventRecord(b, h->stream));
+        return LDPM_OK;
+    };
+    int rc = rec(0, [&]() -> int {
+        cudaError_t e = launch_kick(h->dm, h->stream);
+        return e == cudaSuccess ? LDPM_OK : fail(LDPM_E_CUDA, "kick: %s", cudaGetErrorString(e));
+    });
+    if (rc) return rc;
+    for (int64_t i = 0; i < nsteps; ++i) {
+        const bool lst = i == nsteps - 1;
+        if ((rc = rec(1, [&]() { return launch_facet_any(h, FACET_STEP, nullptr); }))) return rc;
+        if ((rc = rec(2, [&]() { return launch_gather_any(h, lst ? GATHER_STEP_LAST : GATHER_STEP_MID, nullptr); })))
+            return rc;
+    }
+    return LDPM_OK;
+}
+
+int collect_profile(ldpm_ctx *h)
+{
+    for (auto &pr : h->ev_pairs) {
+        float ms = 0;
+        CU(cudaEventSynchronize(h->ev_pool[pr.second + 1]));
+        CU(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
+        h->prof_ms[pr.first] += ms;
+        h->prof_cnt[pr.first] += 1;
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    h->ev_pool.clear();
+    h->ev_pairs.clear();
+    return LDPM_OK;
+}
+
+int check_flag(ldpm_ctx *h)
+{
+    int32_t fl = 0;
+    CU(cudaMemcpyAsync(&fl, h->dm.flag, sizeof(fl), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (fl) return fail(LDPM_E_UNSTABLE, "non-finite velocity or displacement (time step too large?)");
+    return LDPM_OK;
+}
+
+struct DevGuard {
+    int prev = -1;
+    explicit DevGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DevGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Caller-order state <-> internal arrays.
+int download_state(ldpm_ctx *h, std::vector<double> &ps, std::vector<double> *hist5_int)
+{
+    ps.resize(16 * (size_t)h->dm.N);
+    CU(cudaMemcpyAsync(ps.data(), h->dm.pstate, ps.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (hist5_int) {
+        const int64_t Fint = 12 * (int64_t)h->dm.T;
+        double *d5 = nullptr;
+        int rc;
+        if ((rc = dalloc(&d5, 5 * (size_t)Fint))) return rc;
+        cudaError_t e = h->prec == LDPM_MIXED ? launch_hist_to_user<float>(h->dm, d5, h->stream)
+                                              : launch_hist_to_user<double>(h->dm, d5, h->stream);
+        hist5_int->resize(5 * (size_t)Fint);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hist5_int->data(), d5, hist5_int->size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        cudaFree(d5);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(LDPM_E_CUDA, "history download: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    return LDPM_OK;
+}
+
+}  // namespace
+
+// =================================================================================================
+// C ABI
+// =================================================================================================
+extern "C" {
+
+const char *ldpm_last_error(void) { return g_err.c_str(); }
+
+int ldpm_create(const ldpm_geometry *geom, const ldpm_material *mat, const ldpm_options *opt, ldpm_t *out)
+{
+    g_err.clear();
+    if (!geom || !mat || !opt) return fail(LDPM_E_INVALID_ARG, "geometry, material and options are required");
+    try {
+        return create_model(1, geom, mat, opt, out);
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(LDPM_E_CUDA, "unexpected exception in ldpm_create");
+    }
+}
+
+int ldpm_step(ldpm_t h, int64_t nsteps)
+{
+    g_err.clear();
+    if (!h || nsteps < 0) return fail(LDPM_E_INVALID_ARG, "bad handle or nsteps < 0");
+    if (nsteps == 0) return LDPM_OK;
+    DevGuard dg(h->device);
+    try {
+        if (h->prof) return enqueue_profiled(h, nsteps);
+        if (h->graph_chunk < 0) return enqueue_direct(h, nsteps, true, true);
+        int rc;
+        cudaError_t e = launch_kick(h->dm, h->stream);
+        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "kick launch: %s", cudaGetErrorString(e));
+        int64_t mid = nsteps - 1;
+        const int64_t chunk = std::max(1, h->graph_chunk);
+        while (mid > 0) {
+            const int64_t len = std::min(mid, chunk);
+            cudaGraphExec_t ex;
+            if ((rc = graph_for(h, len, &ex))) return rc;
+            CU(cudaGraphLaunch(ex, h->stream));
+            mid -= len;
+        }
+        return enqueue_direct(h, 1, false, true);
+    } catch (...) {
+        return fail(LDPM_E_CUDA, "unexpected exception in ldpm_step");
+    }
+}
+
+int ldpm_sync(ldpm_t h)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    CU(cudaStreamSynchronize(h->stream));
+    return check_flag(h);
+}
+
+int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    try {
+        std::vector<double> ps, h5;
+        int rc = download_state(h, ps, hist5 ? &h5 : nullptr);
+        if (rc) return rc;
+        int64_t st = 0;
+        CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
+        size_t base_p = 0, base_f = 0;
+        for (auto &S : h->sp) {
+            for (int32_t i = 0; i < S.N; ++i) {
+                const size_t P = (size_t)S.p0 + S.inv_p[i];
+                for (int k = 0; k < 6; ++k) {
+                    if (q) q[6 * (base_p + i) + k] = ps[16 * P + 3 + k];
+                    if (v) v[6 * (base_p + i) + k] = ps[16 * P + 9 + k];
+                }
+            }
+            if (hist5)
+                for (int32_t k = 0; k < S.F; ++k) {
+                    const double *src = &h5[5 * (size_t)S.fmap[k]];
+                    double *dst = hist5 + 5 * (base_f + k);
+                    const double sg = S.fswap[k] ? -1.0 : 1.0;
+                    dst[0] = src[0];
+                    dst[1] = sg * src[1];
+                    dst[2] = sg * src[2];
+                    dst[3] = sg * src[3];
+                    dst[4] = src[4];
+                }
+            base_p += S.N;
+            base_f += S.F;
+        }
+        if (step) *step = st;
+        return check_flag(h);
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
+int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *hist5, int64_t step)
+{
+    g_err.clear();
+    if (!h || !q || !v) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL q/v");
+    DevGuard dg(h->device);
+    try {
+        std::vector<double> ps;
+        int rc = download_state(h, ps, nullptr);
+        if (rc) return rc;
+        const int64_t Fint = 12 * (int64_t)h->dm.T;
+        std::vector<double> h5(5 * (size_t)Fint, 0.0);
+        size_t base_p = 0, base_f = 0;
+        for (auto &S : h->sp) {
+            S.W_kin0 = 0.0;
+            for (int32_t i = 0; i < S.N; ++i) {
+                const size_t P = (size_t)S.p0 + S.inv_p[i];
+                for (int k = 0; k < 6; ++k) {
+                    ps[16 * P + 3 + k] = q[6 * (base_p + i) + k];
+                    const double vv = v[6 * (base_p + i) + k];
+                    ps[16 * P + 9 + k] = vv;
+                    S.W_kin0 += 0.5 * vv * vv / h->inv_mass[6 * P + k];
+                }
+            }
+            if (hist5)
+                for (int32_t k = 0; k < S.F; ++k) {
+                    double *dst = &h5[5 * (size_t)S.fmap[k]];
+                    const double *src = hist5 + 5 * (base_f + k);
+                    const double sg = S.fswap[k] ? -1.0 : 1.0;
+                    dst[0] = src[0];
+                    dst[1] = sg * src[1];
+                    dst[2] = sg * src[2];
+                    dst[3] = sg * src[3];
+                    dst[4] = src[4];
+                }
+            base_p += S.N;
+            base_f += S.F;
+        }
+        CU(cudaMemcpy(h->dm.pstate, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemset(h->dm.pdyn, 0, 8 * (size_t)h->dm.N * sizeof(double)));
+        double *d5 = nullptr;
+        if ((rc = dalloc(&d5, 5 * (size_t)Fint))) return rc;
+        cudaError_t e = cudaMemcpy(d5, h5.data(), h5.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = h->prec == LDPM_MIXED ? launch_hist_from_user<float>(h->dm, d5, h->stream)
+                                      : launch_hist_from_user<double>(h->dm, d5, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        cudaFree(d5);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(LDPM_E_CUDA, "history upload: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        CU(cudaMemcpy(h->dm.step, &step, sizeof(step), cudaMemcpyHostToDevice));
+        CU(cudaMemset(h->dm.flag, 0, sizeof(int32_t)));
+        return forces_from_history(h);
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
+static int energy_of(ldpm_t h, int s, double out[4], double reaction[12])
+{
+    const SpecHost &S = h->sp[s];
+    cudaError_t e = launch_energy(h->dm, S.p0, S.p0 + S.N, h->d_partial, h->d_out16, h->stream);
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "energy launch: %s", cudaGetErrorString(e));
+    CU(cudaMemcpyAsync(h->h_out16, h->d_out16, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    const double *r = h->h_out16;
+    const double Wint = r[0], Wext = r[1], Wkin = r[2];
+    if (out) {
+        out[0] = Wext;
+        out[1] = Wint;
+        out[2] = Wkin;
+        const double den = std::fabs(Wext) + S.W_kin0;
+        out[3] = den > 0 ? 100.0 * std::fabs(Wext + S.W_kin0 - Wint - Wkin) / den : 0.0;
+    }
+    if (reaction)
+        for (int k = 0; k < 12; ++k) reaction[k] = r[4 + k];
+    return LDPM_OK;
+}
+
+int ldpm_energy(ldpm_t h, double out[4], double reaction[12])
+{
+    g_err.clear();
+    if (!h || !out) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL out");
+    DevGuard dg(h->device);
+    int rc = energy_of(h, 0, out, reaction);
+    if (rc) return rc;
+    return check_flag(h);
+}
+
+int ldpm_facet_forces(ldpm_t h, double *F3, double *f6)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    try {
+        CU(cudaStreamSynchronize(h->stream));
+        const int64_t Fint = 12 * (int64_t)h->dm.T;
+        std::vector<double> fo(4 * (size_t)Fint), pd(8 * (size_t)h->dm.N);
+        if (h->prec == LDPM_MIXED) {
+            std::vector<float4> t(Fint);
+            CU(cudaMemcpy(t.data(), h->dm.fout, Fint * sizeof(float4), cudaMemcpyDeviceToHost));
+            for (int64_t f = 0; f < Fint; ++f) {
+                fo[4 * f] = t[f].x;
+                fo[4 * f + 1] = t[f].y;
+                fo[4 * f + 2] = t[f].z;
+            }
+        } else {
+            CU(cudaMemcpy(fo.data(), h->dm.fout, Fint * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        CU(cudaMemcpy(pd.data(), h->dm.pdyn, pd.size() * sizeof(double), cudaMemcpyDeviceToHost));
+        size_t base_p = 0, base_f = 0;
+        for (auto &S : h->sp) {
+            if (F3)
+                for (int32_t k = 0; k < S.F; ++k) {
+                    const double sg = S.fswap[k] ? -1.0 : 1.0;
+                    for (int a = 0; a < 3; ++a) F3[3 * (base_f + k) + a] = sg * fo[4 * (size_t)S.fmap[k] + a];
+                }
+            if (f6)
+                for (int32_t i = 0; i < S.N; ++i) {
+                    const size_t P = (size_t)S.p0 + S.inv_p[i];
+                    for (int k = 0; k < 6; ++k) f6[6 * (base_p + i) + k] = pd[8 * P + k];
+                }
+            base_p += S.N;
+            base_f += S.F;
+        }
+        return LDPM_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
+int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_time)
+{
+    g_err.clear();
+    if (!h || !mask || !std::isfinite(ramp_time)) return fail(LDPM_E_INVALID_ARG, "bad handle, mask or ramp_time");
+    if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "ldpm_set_bc applies to single-specimen handles");
+    DevGuard dg(h->device);
+    SpecHost &S = h->sp[0];
+    std::vector<double> bv(6 * (size_t)h->dm.N, 0.0);
+    for (int32_t i = 0; i < S.N; ++i) {
+        const size_t P = (size_t)S.p0 + S.inv_p[i];
+        uint64_t bits = 0;
+        for (int k = 0; k < 6; ++k) {
+            const int mk = mask[6 * (size_t)i + k];
+            if (mk < 0 || mk > 2) return fail(LDPM_E_INVALID_ARG, "bc mask must be 0, 1 or 2");
+            bits |= (uint64_t)mk << (8 * k);
+            bv[6 * P + k] = vel ? vel[6 * (size_t)i + k] : 0.0;
+        }
+        std::memcpy(&h->pconst_h[8 * P + 6], &bits, 8);
+    }
+    S.ramp_time = ramp_time;
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpy(h->dm.pconst, h->pconst_h.data(), h->pconst_h.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.bc_vel, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return update_law(h);
+}
+
+int ldpm_info(ldpm_t h, int64_t info[5], double *dt)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    int64_t N = 0, T = 0, F = 0;
+    for (auto &S : h->sp) {
+        N += S.N;
+        T += S.T;
+        F += S.F;
+    }
+    if (info) {
+        CU(cudaStreamSynchronize(h->stream));
+        int64_t st = 0;
+        CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
+        info[0] = N;
+        info[1] = T;
+        info[2] = F;
+        info[3] = h->prec;
+        info[4] = st;
+    }
+    if (dt) *dt = h->sp[0].dt;
+    return LDPM_OK;
+}
+
+int ldpm_profile(ldpm_t h, int32_t enable)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    if (h->prof) collect_profile(h);
+    h->prof = enable != 0;
+    for (int k = 0; k < 3; ++k) {
+        h->prof_ms[k] = 0;
+        h->prof_cnt[k] = 0;
+    }
+    return LDPM_OK;
+}
+
+int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    int rc = collect_profile(h);
+    if (rc) return rc;
+    for (int k = 0; k < n && k < 3; ++k) {
+        if (ms) ms[k] = h->prof_ms[k];
+        if (count) count[k] = h->prof_cnt[k];
+    }
+    return LDPM_OK;
+}
+
+int64_t ldpm_checkpoint_size(ldpm_t h)
+{
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    const int64_t Fint = 12 * (int64_t)h->dm.T;
+    return (int64_t)(16 + 8) * h->dm.N * 8 + Fint * (int64_t)h->r4size() + 8 + 8 + 8 * (int64_t)h->sp.size();
+}
+
+int ldpm_save_checkpoint(ldpm_t h, void *buf)
+{
+    g_err.clear();
+    if (!h || !buf) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL buffer");
+    DevGuard dg(h->device);
+    char *p = static_cast<char *>(buf);
+    const size_t n_ps = 16 * (size_t)h->dm.N * 8, n_pd = 8 * (size_t)h->dm.N * 8;
+    const size_t n_h = 12 * (size_t)h->dm.T * h->r4size();
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpy(p, h->dm.pstate, n_ps, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(p + n_ps, h->dm.pdyn, n_pd, cudaMemcpyDeviceToHost));
+    CU(cudaMemcpy(p + n_ps + n_pd, h->dm.hist, n_h, cudaMemcpyDeviceToHost));
+    char *q = p + n_ps + n_pd + n_h;
+    CU(cudaMemcpy(q, h->dm.step, 8, cudaMemcpyDeviceToHost));
+    int32_t fl = 0;
+    CU(cudaMemcpy(&fl, h->dm.flag, 4, cudaMemcpyDeviceToHost));
+    int64_t fl64 = fl;
+    std::memcpy(q + 8, &fl64, 8);
+    for (size_t s = 0; s < h->sp.size(); ++s) std::memcpy(q + 16 + 8 * s, &h->sp[s].W_kin0, 8);
+    return LDPM_OK;
+}
+
+int ldpm_load_checkpoint(ldpm_t h, const void *buf)
+{
+    g_err.clear();
+    if (!h || !buf) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL buffer");
+    DevGuard dg(h->device);
+    const char *p = static_cast<const char *>(buf);
+    const size_t n_ps = 16 * (size_t)h->dm.N * 8, n_pd = 8 * (size_t)h->dm.N * 8;
+    const size_t n_h = 12 * (size_t)h->dm.T * h->r4size();
+    CU(cudaStreamSynchronize(h->stream));
+    CU(cudaMemcpy(h->dm.pstate, p, n_ps, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.pdyn, p + n_ps, n_pd, cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.hist, p + n_ps + n_pd, n_h, cudaMemcpyHostToDevice));
+    const char *q = p + n_ps + n_pd + n_h;
+    CU(cudaMemcpy(h->dm.step, q, 8, cudaMemcpyHostToDevice));
+    int64_t fl64;
+    std::memcpy(&fl64, q + 8, 8);
+    int32_t fl = (int32_t)fl64;
+    CU(cudaMemcpy(h->dm.flag, &fl, 4, cudaMemcpyHostToDevice));
+    for (size_t s = 0; s < h->sp.size(); ++s) std::memcpy(&h->sp[s].W_kin0, q + 16 + 8 * s, 8);
+    return LDPM_OK;
+}
+
+void ldpm_destroy(ldpm_t h)
+{
+    if (!h) return;
+    {
+        DevGuard dg(h->device);
+        if (h->stream) cudaStreamSynchronize(h->stream);
+        free_model(h);
+    }
+    delete h;
+}
+
+}  // extern "C"

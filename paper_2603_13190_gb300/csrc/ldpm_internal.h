@@ -1,0 +1,91 @@
+// ldpm_internal.h -- layouts and launcher declarations shared by the host runtime (ldpm_api.cu)
+// and the kernels (ldpm_kernels.cu).  Not part of the public ABI.
+//
+// Device layout (all arrays in the library's internal order: particles and tetrahedra sorted along a
+// Morton curve, facets tetrahedron-major with 12 consecutive slots per tetrahedron):
+//   pstate [N][16] f64  x(3) q(6) v(6) pad      gathered by the facet pass (one 128-byte line)
+//   pdyn   [N][8]  f64  f_asm(6) W_int W_ext     node force sums of the current step, energy sums
+//   pconst [N][8]  f64  1/mass(6) bc-bits spec   per-DOF inverse mass, 8-bit BC code per DOF, specimen
+//   tet    [T]     int4 particle ids of the 4 vertices (-1: padding tetrahedron)
+//   geo    [12T]   R4   c_a (arm from the edge's first vertex to the facet centroid), projected area A
+//   hist   [12T]   R4   t_N, t_M, t_L, e_max
+//   fout   [12T]   R4   facet force acting on the edge's first vertex, 0
+//   row    [N+1]   i32  CSR of facet ends per particle
+//   ent    [2*12T] R4   arm c_s of that end, (facet << 1 | side) stored bit-wise in .w
+// Facet slot s of a tetrahedron belongs to edge e = s / 2 with local vertices
+// (a, b) in ((0,1),(0,2),(0,3),(1,2),(1,3),(2,3)); "I" of the internal facet is vertex a.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ldpm {
+
+struct alignas(32) double4a {
+    double x, y, z, w;
+};
+
+template <class R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+    using type = float4;
+};
+template <>
+struct Vec4<double> {
+    using type = double4a;
+};
+template <class R>
+using R4 = typename Vec4<R>::type;
+
+// Constants of the facet law in the facet pass's precision, derived once on the host.
+template <class R>
+struct LawConst {
+    R E0, alpha, inv_alpha, sigma_t, four_alpha_over_r2, Hs_over_alpha, n_t, l_t;
+    R sigma_c0, Hc0, Hc1, kc1, kc2, ec0, ec1, eV0, beta, Ed;
+    R mu_diff_sN0, mu_inf, inv_sigma_N0, sigma_s;
+    R dt;
+    R tiny_strain;  // fracture branch: effective strains below this respond elastically
+    int32_t elastic;
+};
+
+// Per-specimen time integration constants (FP64).
+struct SpecDyn {
+    double dt, ramp_time;
+};
+
+enum FacetMode : int { FACET_STEP = 0, FACET_FROM_HIST = 1, FACET_ELASTIC = 2 };
+enum GatherMode : int { GATHER_ASSEMBLE = 0, GATHER_STEP_MID = 1, GATHER_STEP_LAST = 2 };
+
+struct DeviceModel {
+    int32_t N = 0, T = 0;     // T includes padding tetrahedra
+    int32_t n_spec = 0;
+    int32_t tets_per_block = 32;
+    double *pstate = nullptr, *pdyn = nullptr, *pconst = nullptr;
+    double *bc_vel = nullptr, *f_ext = nullptr;
+    int4 *tet = nullptr;
+    void *geo = nullptr, *hist = nullptr, *fout = nullptr, *ent = nullptr;
+    int32_t *row = nullptr;
+    int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)
+    void *law = nullptr;            // LawConst<R>[n_spec]
+    SpecDyn *spec = nullptr;        // [n_spec]
+    int64_t *step = nullptr;        // step counter (one for all specimens)
+    int32_t *flag = nullptr;        // non-finite state seen
+};
+
+// Launchers (ldpm_kernels.cu).  All enqueue on `s` and return the launch error.
+cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s);
+template <class R>
+cudaError_t launch_facet(const DeviceModel &m, int mode, const double *pstate_override, cudaStream_t s);
+template <class R>
+cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStream_t s);
+// Energy sums over particles [p0, p1): out16 = W_int, W_ext, W_kin, pad, reaction fixed(6),
+// reaction prescribed(6).  `partial` holds ceil((p1 - p0) / 256) * 16 doubles.
+cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, double *out16,
+                          cudaStream_t s);
+template <class R>
+cudaError_t launch_hist_to_user(const DeviceModel &m, double *out5, cudaStream_t s);
+template <class R>
+cudaError_t launch_hist_from_user(const DeviceModel &m, const double *in5, cudaStream_t s);
+
+}  // namespace ldpm

@@ -1,0 +1,687 @@
+// ldpm_kernels.cu -- sm_103a kernels of the LDPM explicit central-difference step.
+//
+// One step (paper Sec. 3, central difference with lumped mass) is two launches in steady state:
+//   facet_kernel   per facet: rigid-body jump and strain (Sec. 2, Eq. (1)), per-tetrahedron
+//                  volumetric strain (App. A.2 e_V), the Appendix A law, force A P t (Eq. (2));
+//   gather_kernel  per particle: fixed-order sum of its facet ends (Eq. (2a)-(2b)), then the second
+//                  half kick of this step, the energy increments, and the first half kick and drift
+//                  of the next step.
+// The pass is bound by HBM bandwidth: no tensor cores (no dense contraction), no float atomics.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ldpm_internal.h"
+
+namespace ldpm {
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+
+// ------------------------------------------------------------------------------------------------
+// Small vector helpers.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+struct V3 {
+    R x, y, z;
+};
+template <class R>
+__device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <class R>
+__device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <class R>
+__device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <class R>
+__device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <class R>
+__device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b)
+{
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
+
+// Tangent pair (m, l) of a unit normal n: the branch-free orthonormal basis of Duff et al.,
+// "Building an Orthonormal Basis, Revisited" (JCGT 6(1), 2017).  Any orthonormal tangents are
+// allowed (paper Sec. 2); this choice is continuous except across n_z = 0.
+template <class R>
+__device__ __forceinline__ void tangent_frame(V3<R> n, V3<R> &m, V3<R> &l)
+{
+    const R sgn = copysign(R(1), n.z);
+    const R a = R(-1) / (sgn + n.z);
+    const R b = n.x * n.y * a;
+    m = {R(1) + sgn * n.x * n.x * a, sgn * b, -sgn * n.x};
+    l = {b, sgn + n.y * n.y * a, -n.y};
+}
+
+// ------------------------------------------------------------------------------------------------
+// Appendix A constitutive update of one facet.  e: strain, de: its increment over this step, eV:
+// volumetric strain of the tetrahedron, l: facet (edge) length; t/emax: previous history in,
+// new history out.
+// ------------------------------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void facet_law(const LawConst<R> &c, R l, V3<R> e, V3<R> de, R eV, R &tN, R &tM,
+                                          R &tL, R &emax)
+{
+    const R E0 = c.E0, alpha = c.alpha;
+    if (c.elastic) {  // Sec. 2: t = E0 diag(1, alpha, alpha) e
+        tN = E0 * e.x;
+        tM = alpha * E0 * e.y;
+        tL = alpha * E0 * e.z;
+        return;
+    }
+    if (e.x > R(0)) {
+        // App. A.1 fracture.  Effective strain, coupling angle omega (sin = e_N / e,
+        // cos = sqrt(alpha e_T^2) / e), strength sigma_0(omega) written as
+        // 2 sigma_t / (sin + sqrt(sin^2 + 4 alpha cos^2 / r_st^2)) (the paper's expression with
+        // numerator and denominator multiplied by the conjugate; finite at omega = pi/2).
+        const R aT2 = alpha * (e.y * e.y + e.z * e.z);
+        const R eeff = sqrt(e.x * e.x + aT2);
+        if (eeff < c.tiny_strain) {
+            // t / e is 0/0 at vanishing strain (its squares underflow first); the elastic limit
+            // t = E e applies.  Reached ahead of a loading wave, where strains decay to ~0.
+            tN = E0 * e.x;
+            tM = alpha * E0 * e.y;
+            tL = alpha * E0 * e.z;
+            emax = emax > eeff ? emax : eeff;
+            return;
+        }
+        const R saT = sqrt(aT2);
+        const R omega = atan2(e.x, saT);
+        const R inv_e = R(1) / eeff;
+        const R sn = e.x * inv_e, cs = saT * inv_e;
+        const R sigma0 = R(2) * c.sigma_t / (sn + sqrt(sn * sn + c.four_alpha_over_r2 * cs * cs));
+        // H_t = 2 E0 / (l_t / l - 1) = 2 E0 l / (l_t - l); H_0 = H_s/alpha + (H_t - H_s/alpha)(2 omega/pi)^n_t
+        const R Ht = R(2) * E0 * l / (c.l_t - l);
+        const R H0 = c.Hs_over_alpha + (Ht - c.Hs_over_alpha) * pow(omega * R(2.0 / kPi), c.n_t);
+        const R e0 = sigma0 / E0;
+        emax = emax > eeff ? emax : eeff;
+        const R over = emax - e0 > R(0) ? emax - e0 : R(0);
+        const R sigma_bt = sigma0 * exp(-H0 * over / sigma0);
+        // t = t_old + E0 (e - e_old).  The effective-strain difference is formed from the increment:
+        // e^2 - e_old^2 = sum_i w_i de_i (2 e_i - de_i) with w = (1, alpha, alpha), divided by
+        // (e + e_old) -- algebraically the same, free of the cancellation of two nearby roots.
+        const V3<R> ep = e - de;
+        const R e_old = sqrt(ep.x * ep.x + alpha * (ep.y * ep.y + ep.z * ep.z));
+        const R num = de.x * (e.x + ep.x) + alpha * (de.y * (e.y + ep.y) + de.z * (e.z + ep.z));
+        const R d_eff = num / (eeff + e_old);
+        const R t_old = sqrt(tN * tN + (tM * tM + tL * tL) * c.inv_alpha);
+        R t = t_old + E0 * d_eff;
+        t = t < R(0) ? R(0) : t;
+        t = t > sigma_bt ? sigma_bt : t;
+        const R r = t * inv_e;
+        tN = r * e.x;
+        tM = alpha * r * e.y;
+        tL = alpha * r * e.z;
+        return;
+    }
+    // App. A.2 compression: t_N incrementally elastic (E_Nc), -sigma_bc <= t_N <= 0.
+    const R ENc = (-tN <= c.sigma_c0) ? E0 : c.Ed;
+    R tn = tN + ENc * de.x;
+    const R eD = e.x - eV;
+    const R eDV = eV + c.beta * eD;
+    const R rDV = (eV <= R(0)) ? -fabs(eD) / (eV - c.eV0) : fabs(eD) / c.eV0;
+    const R mac = rDV - c.kc1 > R(0) ? rDV - c.kc1 : R(0);
+    const R Hc = (c.Hc0 - c.Hc1) / (R(1) + c.kc2 * mac) + c.Hc1;
+    R sigma_bc;
+    if (-eDV <= R(0)) {
+        sigma_bc = c.sigma_c0;
+    } else if (-eDV <= c.ec1) {
+        const R o = -eDV - c.ec0 > R(0) ? -eDV - c.ec0 : R(0);
+        sigma_bc = c.sigma_c0 + o * Hc;
+    } else {
+        const R sigma_c1 = c.sigma_c0 + (c.ec1 - c.ec0) * Hc;
+        sigma_bc = sigma_c1 * exp((-eDV - c.ec1) * Hc / sigma_c1);
+    }
+    tn = tn < -sigma_bc ? -sigma_bc : tn;
+    tn = tn > R(0) ? R(0) : tn;
+    // App. A.3 friction: elastic shear trial, radial return onto sqrt(t_M^2 + t_L^2) = sigma_bs(t_N).
+    R tm = tM + alpha * E0 * de.y;
+    R tl = tL + alpha * E0 * de.z;
+    const R sigma_bs = c.sigma_s + c.mu_diff_sN0 - c.mu_inf * tn - c.mu_diff_sN0 * exp(tn * c.inv_sigma_N0);
+    const R tau2 = tm * tm + tl * tl;
+    if (tau2 > sigma_bs * sigma_bs) {
+        const R s = sigma_bs * rsqrt_(tau2);
+        tm *= s;
+        tl *= s;
+    }
+    tN = tn;
+    tM = tm;
+    tL = tl;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Facet pass.  A block owns TETS consecutive tetrahedra (12 * TETS facets, one thread each).
+// Phase A: 4 threads per tetrahedron gather the vertex records (x, q, v; one 128-byte line each),
+// form FP64 differences to vertex 0 of the tetrahedron, round them to R and park them in shared
+// memory, and compute the tetrahedron's volumetric strain.  Phase B: one thread per facet.
+// The facet's own geometry and history are loaded before phase A so their HBM latency overlaps
+// the gathers.
+// ------------------------------------------------------------------------------------------------
+constexpr int kVtx = 15;  // dx(3) du(3) dv(3) theta(3) omega(3)
+
+template <class R, int MODE, int TETS>
+__global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const double *__restrict__ pst)
+{
+    __shared__ R sv[TETS * 4][kVtx];  // odd row stride: conflict-free per-lane writes
+    __shared__ R seV[TETS];
+    __shared__ int sok[TETS];
+    using T4 = R4<R>;
+    const T4 *__restrict__ geo = static_cast<const T4 *>(m.geo);
+    T4 *__restrict__ hist = static_cast<T4 *>(m.hist);
+    T4 *__restrict__ fout = static_cast<T4 *>(m.fout);
+    const LawConst<R> *__restrict__ lawc = static_cast<const LawConst<R> *>(m.law);
+
+    const int tid = threadIdx.x;
+    const int64_t tet0 = (int64_t)blockIdx.x * TETS;
+    if (MODE == FACET_STEP && blockIdx.x == 0 && tid == 0) *m.step += 1;
+
+    // ---- prefetch this thread's facet data
+    const int j = tid / 12;
+    const int slot = tid - 12 * j;
+    const int64_t f = tet0 * 12 + tid;
+    const bool valid = tet0 + j < m.T;
+    T4 g{}, h{};
+    if (valid) {
+        g = geo[f];
+        if (MODE != FACET_ELASTIC) h = hist[f];
+    }
+
+    // ---- phase A: vertex records -> shared memory, e_V per tetrahedron
+    if (tid < 4 * TETS) {
+        const int jt = tid >> 2, vi = tid & 3;
+        const int64_t tt = tet0 + jt;
+        int p = -1;
+        if (tt < m.T) p = reinterpret_cast<const int *>(m.tet)[4 * tt + vi];
+        double rec[15];
+        if (p >= 0) {
+            const double2 *r2 = reinterpret_cast<const double2 *>(pst + 16 * (int64_t)p);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) {
+                const double2 w = r2[k];
+                rec[2 * k] = w.x;
+                rec[2 * k + 1] = w.y;
+            }
+            rec[14] = pst[16 * (int64_t)p + 14];
+        } else {
+#pragma unroll
+            for (int k = 0; k < 15; ++k) rec[k] = 0.0;
+        }
+        // rec: x 0..2, u 3..5, theta 6..8, v 9..11, omega 12..14
+        const int base = (threadIdx.x & 31) & ~3;
+        double ref[9];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            ref[k] = __shfl_sync(0xffffffffu, rec[k], base);
+            ref[3 + k] = __shfl_sync(0xffffffffu, rec[3 + k], base);
+            ref[6 + k] = __shfl_sync(0xffffffffu, rec[9 + k], base);
+        }
+        R *o = sv[tid];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            o[k] = R(rec[k] - ref[k]);              // dx
+            o[3 + k] = R(rec[3 + k] - ref[3 + k]);  // du
+            o[6 + k] = R(rec[9 + k] - ref[6 + k]);  // dv
+            o[9 + k] = R(rec[6 + k]);               // theta
+            o[12 + k] = R(rec[12 + k]);             // omega
+        }
+        // e_V = (1/3) div u of the linear tetrahedron.  With D = [dx1 dx2 dx3], grad N_i (i = 1..3)
+        // are the rows of D^-1 = [dx2 x dx3; dx3 x dx1; dx1 x dx2] / det D, and vertex 0 carries no
+        // displacement difference.  Lane i >= 1 forms its own term du_i . (dx_i1 x dx_i2).
+        const V3<R> dxs = {o[0], o[1], o[2]};
+        const V3<R> dus = {o[3], o[4], o[5]};
+        const int i1 = vi == 3 ? 1 : vi + 1;
+        const int i2 = i1 == 3 ? 1 : i1 + 1;
+        V3<R> a1, a2;
+        a1.x = __shfl_sync(0xffffffffu, dxs.x, base + i1);
+        a1.y = __shfl_sync(0xffffffffu, dxs.y, base + i1);
+        a1.z = __shfl_sync(0xffffffffu, dxs.z, base + i1);
+        a2.x = __shfl_sync(0xffffffffu, dxs.x, base + i2);
+        a2.y = __shfl_sync(0xffffffffu, dxs.y, base + i2);
+        a2.z = __shfl_sync(0xffffffffu, dxs.z, base + i2);
+        const V3<R> cr = cross(a1, a2);
+        R term = vi == 0 ? R(0) : dot(dus, cr);
+        R det = vi == 0 ? R(0) : dot(dxs, cr);
+        term += __shfl_xor_sync(0xffffffffu, term, 1);
+        term += __shfl_xor_sync(0xffffffffu, term, 2);
+        det = __shfl_sync(0xffffffffu, det, base + 1);
+        if (vi == 0) {
+            seV[jt] = (p >= 0 && det != R(0)) ? term / (R(3) * det) : R(0);
+            sok[jt] = p >= 0;
+        }
+    }
+    __syncthreads();
+    if (!valid || !sok[j]) return;
+
+    // ---- phase B: one facet
+    const int e = slot >> 1;
+    const int va = (0x211000 >> (4 * e)) & 0xF;
+    const int vb = (0x332321 >> (4 * e)) & 0xF;
+    const R *A = sv[4 * j + va];
+    const R *B = sv[4 * j + vb];
+    const V3<R> d = {B[0] - A[0], B[1] - A[1], B[2] - A[2]};
+    const R inv_l = rsqrt_(dot(d, d));
+    const R l = dot(d, d) * inv_l;
+    const V3<R> n = inv_l * d;
+    V3<R> mt, lt;
+    tangent_frame(n, mt, lt);
+    const V3<R> ca = {g.x, g.y, g.z};
+    const V3<R> cb = ca - d;
+    R tN, tM, tL, emax;
+    const int sp = m.tile_spec ? m.tile_spec[blockIdx.x] : 0;
+    const LawConst<R> &c = lawc[sp];
+    if (MODE == FACET_FROM_HIST) {
+        tN = h.x;
+        tM = h.y;
+        tL = h.z;
+    } else {
+        const V3<R> thA = {A[9], A[10], A[11]}, thB = {B[9], B[10], B[11]};
+        const V3<R> du = {B[3] - A[3], B[4] - A[4], B[5] - A[5]};
+        const V3<R> jump = du + cross(thB, cb) - cross(thA, ca);
+        const V3<R> e3 = {dot(n, jump) * inv_l, dot(mt, jump) * inv_l, dot(lt, jump) * inv_l};
+        if (MODE == FACET_ELASTIC) {
+            tN = c.E0 * e3.x;
+            tM = c.alpha * c.E0 * e3.y;
+            tL = c.alpha * c.E0 * e3.z;
+        } else {
+            const V3<R> omA = {A[12], A[13], A[14]}, omB = {B[12], B[13], B[14]};
+            const V3<R> dv = {B[6] - A[6], B[7] - A[7], B[8] - A[8]};
+            const V3<R> djump = dv + cross(omB, cb) - cross(omA, ca);
+            const R sdt = c.dt * inv_l;
+            const V3<R> de3 = {dot(n, djump) * sdt, dot(mt, djump) * sdt, dot(lt, djump) * sdt};
+            tN = h.x;
+            tM = h.y;
+            tL = h.z;
+            emax = h.w;
+            facet_law(c, l, e3, de3, seV[j], tN, tM, tL, emax);
+            T4 hn;
+            hn.x = tN;
+            hn.y = tM;
+            hn.z = tL;
+            hn.w = emax;
+            hist[f] = hn;
+        }
+    }
+    const R Ar = g.w;
+    T4 F;
+    F.x = Ar * (tN * n.x + tM * mt.x + tL * lt.x);
+    F.y = Ar * (tN * n.y + tM * mt.y + tL * lt.y);
+    F.z = Ar * (tN * n.z + tM * mt.z + tL * lt.z);
+    F.w = R(0);
+    fout[f] = F;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Particle pass: one warp per particle sums its facet ends in CSR order (Eq. (2a)-(2b)), then
+// lanes 0..5 update one DOF each.
+// ------------------------------------------------------------------------------------------------
+__device__ __forceinline__ double ramp(double t, double T)
+{
+    if (T <= 0.0) return 1.0;
+    const double r = t / T;
+    return r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+}
+
+__device__ __forceinline__ int entry_bits(float w) { return __float_as_int(w); }
+__device__ __forceinline__ int64_t entry_bits(double w) { return __double_as_longlong(w); }
+
+template <class R, int MODE>
+__global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__restrict__ out6)
+{
+    using T4 = R4<R>;
+    const T4 *__restrict__ ent = static_cast<const T4 *>(m.ent);
+    const T4 *__restrict__ fout = static_cast<const T4 *>(m.fout);
+    const int lane = threadIdx.x & 31;
+    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (p >= m.N) return;
+    const int r0 = m.row[p], r1 = m.row[p + 1];
+    R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
+    for (int r = r0 + lane; r < r1; r += 32) {
+        const T4 en = ent[r];
+        const int64_t bits = entry_bits(en.w);
+        const T4 F = fout[bits >> 1];
+        const R sg = (bits & 1) ? R(-1) : R(1);
+        const V3<R> Fs = {sg * F.x, sg * F.y, sg * F.z};
+        const V3<R> mo = cross(V3<R>{en.x, en.y, en.z}, Fs);
+        a0 += Fs.x;
+        a1 += Fs.y;
+        a2 += Fs.z;
+        a3 += mo.x;
+        a4 += mo.y;
+        a5 += mo.z;
+    }
+    double s[6] = {double(a0), double(a1), double(a2), double(a3), double(a4), double(a5)};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
+    // lanes 0..5 own one DOF each; the other lanes mirror DOF 0 and store nothing
+    const bool act = lane < 6;
+    double fa_new = s[0];
+#pragma unroll
+    for (int k = 1; k < 6; ++k)
+        if (lane == k) fa_new = s[k];
+    if (MODE == GATHER_ASSEMBLE) {
+        if (act) out6[6 * p + lane] = fa_new;
+        return;
+    }
+    // ---- velocity-form central difference for DOF d (state on entry: q_{n+1}, v_{n+1/2}, f_n)
+    const int d = act ? lane : 0;
+    double *ps = m.pstate + 16 * p;
+    double *pd = m.pdyn + 8 * p;
+    const double *pc = m.pconst + 8 * p;
+    const double im = pc[d];
+    const uint64_t bcbits = (uint64_t)__double_as_longlong(pc[6]);
+    const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
+    const int sp = (int)__double_as_longlong(pc[7]);
+    const double dt = m.spec[sp].dt, Tr = m.spec[sp].ramp_time;
+    const int64_t n1 = *m.step;
+    const double t1 = (double)n1 * dt;
+    const double t0 = (double)(n1 - 1) * dt;
+    const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
+    const double vh = ps[9 + d];
+    const double fa_old = pd[d];
+    const double dq = dt * vh;
+    double g_old, g_new, v_new, v_next;
+    if (mask == 0) {
+        g_old = fe;
+        g_new = fe;
+        const double a = (fe + fa_new) * im;
+        v_new = vh + 0.5 * dt * a;
+        v_next = v_new + 0.5 * dt * a;
+    } else if (mask == 1) {
+        g_old = -fa_old;
+        g_new = -fa_new;
+        v_new = 0.0;
+        v_next = 0.0;
+    } else {
+        const double vb = m.bc_vel[6 * p + d];
+        const double mass = 1.0 / im;
+        const double a_old = vb * (ramp(t0 + 0.5 * dt, Tr) - ramp(t0 - 0.5 * dt, Tr)) / dt;
+        const double a_new = vb * (ramp(t1 + 0.5 * dt, Tr) - ramp(t1 - 0.5 * dt, Tr)) / dt;
+        g_old = mass * a_old - fa_old;
+        g_new = mass * a_new - fa_new;
+        v_new = vb * ramp(t1, Tr);
+        v_next = vb * ramp(t1 + 0.5 * dt, Tr);
+    }
+    double dWe = act ? 0.5 * (g_old + g_new) * dq : 0.0;
+    double dWi = act ? 0.5 * (-fa_old - fa_new) * dq : 0.0;
+    double q = ps[3 + d];
+    double v_store = v_new;
+    if (MODE != GATHER_STEP_LAST) {
+        v_store = v_next;
+        q += dt * v_next;
+    }
+    // sum the six DOF contributions into lane 0 (lanes 6, 7 hold zeros)
+#pragma unroll
+    for (int off = 4; off > 0; off >>= 1) {
+        dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
+        dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
+    }
+    if (act) {
+        pd[d] = fa_new;
+        if (MODE != GATHER_STEP_LAST) ps[3 + d] = q;
+        ps[9 + d] = v_store;
+        if (!isfinite(v_store) || !isfinite(q)) *(volatile int32_t *)m.flag = 1;
+    }
+    if (lane == 0) {
+        pd[6] += dWi;
+        pd[7] += dWe;
+    }
+}
+
+// First half kick and drift of a stepping call: v_{n+1/2} = v_n + dt/2 a_n, q_{n+1} = q_n + dt v_{n+1/2}.
+__global__ void __launch_bounds__(256) kick_kernel(DeviceModel m)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * (int64_t)m.N) return;
+    const int64_t p = i / 6;
+    const int d = (int)(i - 6 * p);
+    double *ps = m.pstate + 16 * p;
+    const double *pc = m.pconst + 8 * p;
+    const int mask = (int)(((uint64_t)__double_as_longlong(pc[6]) >> (8 * d)) & 0xffu);
+    const int sp = (int)__double_as_longlong(pc[7]);
+    const double dt = m.spec[sp].dt;
+    const double t = (double)(*m.step) * dt;
+    double vh;
+    if (mask == 0) {
+        const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
+        vh = ps[9 + d] + 0.5 * dt * (fe + m.pdyn[8 * p + d]) * pc[d];
+    } else if (mask == 1) {
+        vh = 0.0;
+    } else {
+        vh = m.bc_vel[6 * p + d] * ramp(t + 0.5 * dt, m.spec[sp].ramp_time);
+    }
+    ps[9 + d] = vh;
+    ps[3 + d] += dt * vh;
+}
+
+// Energy sums over particles [p0, p1) (per block, fixed order), then one block adds the partials.
+__global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, int32_t p1, double *partial)
+{
+    __shared__ double red[256][16];
+    const int tid = threadIdx.x;
+    const int64_t p = (int64_t)p0 + (int64_t)blockIdx.x * 256 + tid;
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    if (p < p1) {
+        const double *ps = m.pstate + 16 * p;
+        const double *pd = m.pdyn + 8 * p;
+        const double *pc = m.pconst + 8 * p;
+        const uint64_t bcbits = (uint64_t)__double_as_longlong(pc[6]);
+        const int sp = (int)__double_as_longlong(pc[7]);
+        const double dt = m.spec[sp].dt, Tr = m.spec[sp].ramp_time;
+        const double t = (double)(*m.step) * dt;
+        acc[0] = pd[6];
+        acc[1] = pd[7];
+        for (int d = 0; d < 6; ++d) {
+            const double mass = 1.0 / pc[d];
+            const double v = ps[9 + d];
+            acc[2] += 0.5 * mass * v * v;
+            const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
+            if (mask == 1) {
+                acc[4 + d] += -pd[d];
+            } else if (mask == 2) {
+                const double vb = m.bc_vel[6 * p + d];
+                const double a = vb * (ramp(t + 0.5 * dt, Tr) - ramp(t - 0.5 * dt, Tr)) / dt;
+                acc[10 + d] += mass * a - pd[d];
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 16; ++k) red[tid][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) red[tid][k] += red[tid + w][k];
+        __syncthreads();
+    }
+    if (tid < 16) partial[16 * (int64_t)blockIdx.x + tid] = red[0][tid];
+}
+
+__global__ void __launch_bounds__(256) energy_final_kernel(const double *partial, int32_t nb, double *out16)
+{
+    __shared__ double red[256][16];
+    const int tid = threadIdx.x;
+    double acc[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
+    for (int b = tid; b < nb; b += 256)
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc[k] += partial[16 * (int64_t)b + k];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) red[tid][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w)
+#pragma unroll
+            for (int k = 0; k < 16; ++k) red[tid][k] += red[tid + w][k];
+        __syncthreads();
+    }
+    if (tid < 16) out16[tid] = red[0][tid];
+}
+
+// History <-> caller format (t_N, global tangential traction, e_max), in the internal facet order.
+// The frame is rebuilt from the particle positions exactly as the facet pass forms it.
+template <class R>
+__device__ __forceinline__ bool facet_frame_of(const DeviceModel &m, int64_t f, V3<R> &n, V3<R> &mt, V3<R> &lt)
+{
+    const int64_t tt = f / 12;
+    const int e = (int)(f - 12 * tt) >> 1;
+    const int va = (0x211000 >> (4 * e)) & 0xF;
+    const int vb = (0x332321 >> (4 * e)) & 0xF;
+    const int *tv = reinterpret_cast<const int *>(m.tet) + 4 * tt;
+    const int p0 = tv[0], pa = tv[va], pb = tv[vb];
+    if (p0 < 0) return false;
+    const double *x0 = m.pstate + 16 * (int64_t)p0, *xa = m.pstate + 16 * (int64_t)pa,
+                 *xb = m.pstate + 16 * (int64_t)pb;
+    const V3<R> dxa = {R(xa[0] - x0[0]), R(xa[1] - x0[1]), R(xa[2] - x0[2])};
+    const V3<R> dxb = {R(xb[0] - x0[0]), R(xb[1] - x0[1]), R(xb[2] - x0[2])};
+    const V3<R> d = dxb - dxa;
+    const R inv_l = rsqrt_(dot(d, d));
+    n = inv_l * d;
+    tangent_frame(n, mt, lt);
+    return true;
+}
+
+template <class R>
+__global__ void hist_to_user_kernel(DeviceModel m, double *__restrict__ out5)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= 12 * (int64_t)m.T) return;
+    V3<R> n, mt, lt;
+    const R4<R> h = static_cast<const R4<R> *>(m.hist)[f];
+    double *o = out5 + 5 * f;
+    if (!facet_frame_of<R>(m, f, n, mt, lt)) {
+        for (int k = 0; k < 5; ++k) o[k] = 0.0;
+        return;
+    }
+    o[0] = double(h.x);
+    o[1] = double(h.y) * double(mt.x) + double(h.z) * double(lt.x);
+    o[2] = double(h.y) * double(mt.y) + double(h.z) * double(lt.y);
+    o[3] = double(h.y) * double(mt.z) + double(h.z) * double(lt.z);
+    o[4] = double(h.w);
+}
+
+template <class R>
+__global__ void hist_from_user_kernel(DeviceModel m, const double *__restrict__ in5)
+{
+    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (f >= 12 * (int64_t)m.T) return;
+    V3<R> n, mt, lt;
+    R4<R> h;
+    h.x = h.y = h.z = h.w = R(0);
+    if (facet_frame_of<R>(m, f, n, mt, lt)) {
+        const double *u = in5 + 5 * f;
+        h.x = R(u[0]);
+        h.y = R(u[1] * double(mt.x) + u[2] * double(mt.y) + u[3] * double(mt.z));
+        h.z = R(u[1] * double(lt.x) + u[2] * double(lt.y) + u[3] * double(lt.z));
+        h.w = R(u[4]);
+    }
+    static_cast<R4<R> *>(m.hist)[f] = h;
+}
+
+template <class R, int MODE>
+cudaError_t launch_facet_tpb(const DeviceModel &m, const double *pst, cudaStream_t s)
+{
+    const int tpb = m.tets_per_block;
+    const unsigned blocks = (unsigned)((m.T + tpb - 1) / tpb);
+    if (blocks == 0) return cudaSuccess;
+    switch (tpb) {
+    case 8:
+        facet_kernel<R, MODE, 8><<<blocks, 96, 0, s>>>(m, pst);
+        break;
+    case 16:
+        facet_kernel<R, MODE, 16><<<blocks, 192, 0, s>>>(m, pst);
+        break;
+    default:
+        facet_kernel<R, MODE, 32><<<blocks, 384, 0, s>>>(m, pst);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s)
+{
+    const int64_t n = 6 * (int64_t)m.N;
+    if (n == 0) return cudaSuccess;
+    kick_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_facet(const DeviceModel &m, int mode, const double *pstate_override, cudaStream_t s)
+{
+    const double *pst = pstate_override ? pstate_override : m.pstate;
+    switch (mode) {
+    case FACET_FROM_HIST:
+        return launch_facet_tpb<R, FACET_FROM_HIST>(m, pst, s);
+    case FACET_ELASTIC:
+        return launch_facet_tpb<R, FACET_ELASTIC>(m, pst, s);
+    default:
+        return launch_facet_tpb<R, FACET_STEP>(m, pst, s);
+    }
+}
+
+template <class R>
+cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
+{
+    const int64_t threads = 32 * (int64_t)m.N;
+    if (threads == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    switch (mode) {
+    case GATHER_ASSEMBLE:
+        gather_kernel<R, GATHER_ASSEMBLE><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    case GATHER_STEP_LAST:
+        gather_kernel<R, GATHER_STEP_LAST><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    default:
+        gather_kernel<R, GATHER_STEP_MID><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, double *out16,
+                          cudaStream_t s)
+{
+    const int32_t nb = (p1 - p0 + 255) / 256;
+    if (nb <= 0) return cudaMemsetAsync(out16, 0, 16 * sizeof(double), s);
+    energy_kernel<<<nb, 256, 0, s>>>(m, p0, p1, partial);
+    energy_final_kernel<<<1, 256, 0, s>>>(partial, nb, out16);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_hist_to_user(const DeviceModel &m, double *out5, cudaStream_t s)
+{
+    const int64_t n = 12 * (int64_t)m.T;
+    if (n == 0) return cudaSuccess;
+    hist_to_user_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, out5);
+    return cudaGetLastError();
+}
+
+template <class R>
+cudaError_t launch_hist_from_user(const DeviceModel &m, const double *in5, cudaStream_t s)
+{
+    const int64_t n = 12 * (int64_t)m.T;
+    if (n == 0) return cudaSuccess;
+    hist_from_user_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, in5);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_facet<float>(const DeviceModel &, int, const double *, cudaStream_t);
+template cudaError_t launch_facet<double>(const DeviceModel &, int, const double *, cudaStream_t);
+template cudaError_t launch_gather<float>(const DeviceModel &, int, double *, cudaStream_t);
+template cudaError_t launch_gather<double>(const DeviceModel &, int, double *, cudaStream_t);
+template cudaError_t launch_hist_to_user<float>(const DeviceModel &, double *, cudaStream_t);
+template cudaError_t launch_hist_to_user<double>(const DeviceModel &, double *, cudaStream_t);
+template cudaError_t launch_hist_from_user<float>(const DeviceModel &, const double *, cudaStream_t);
+template cudaError_t launch_hist_from_user<double>(const DeviceModel &, const double *, cudaStream_t);
+
+}  // namespace ldpm

@@ -1,0 +1,285 @@
+"""Thin ctypes binding of libldpm.so (include/ldpm.h): the same entry points, argument marshalling only.
+
+Every computation happens in the CUDA library.  If the library is missing or cannot be loaded the
+import of this module's functions raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LDPM_OK = 0
+ERRORS = {
+    -1: "LDPM_E_INVALID_ARG",
+    -2: "LDPM_E_BAD_GEOMETRY",
+    -3: "LDPM_E_CUDA",
+    -4: "LDPM_E_OOM",
+    -5: "LDPM_E_UNSTABLE",
+    -6: "LDPM_E_TIMEOUT",
+    -7: "LDPM_E_UNSUPPORTED",
+}
+LDPM_FP64, LDPM_MIXED = 0, 1
+MATERIAL_FIELDS = ("rho", "E0", "alpha", "sigma_t", "l_t", "r_st", "n_t", "sigma_c0", "Hc0_E0", "Hc1_E0",
+                   "kc0", "kc1", "kc2", "kc3", "mu0", "mu_inf", "sigma_N0", "Ed_E0", "beta", "k_t", "r_s")
+
+
+class LdpmError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__("%s failed: %s (%s)" % (where, ERRORS.get(code, code), msg))
+        self.code = code
+
+
+class Geometry(C.Structure):
+    _fields_ = [("n_particles", C.c_int32), ("n_tets", C.c_int32), ("n_facets", C.c_int32),
+                ("x", C.c_void_p), ("diameter", C.c_void_p), ("tet", C.c_void_p), ("facet_pi", C.c_void_p),
+                ("facet_pj", C.c_void_p), ("facet_tet", C.c_void_p), ("facet_vtx", C.c_void_p),
+                ("mass", C.c_void_p), ("inertia", C.c_void_p)]
+
+
+class Material(C.Structure):
+    _fields_ = [(f, C.c_double) for f in MATERIAL_FIELDS] + [("elastic", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("graph_chunk", C.c_int32), ("dt", C.c_double), ("dt_factor", C.c_double),
+                ("cuda_stream", C.c_void_p), ("bc_mask", C.c_void_p), ("bc_vel", C.c_void_p),
+                ("ramp_time", C.c_double), ("v0", C.c_void_p), ("f_ext", C.c_void_p), ("device", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libldpm.so (building it first if the sources are newer).  Raises if that fails."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise ImportError("libldpm.so is missing at %s" % path)
+        L = C.CDLL(path)
+        P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+        sig = {
+            "ldpm_create": ([P, P, P, P], C.c_int),
+            "ldpm_step": ([P, I64], C.c_int),
+            "ldpm_sync": ([P], C.c_int),
+            "ldpm_get_state": ([P, P, P, P, P], C.c_int),
+            "ldpm_set_state": ([P, P, P, P, I64], C.c_int),
+            "ldpm_energy": ([P, P, P], C.c_int),
+            "ldpm_facet_forces": ([P, P, P], C.c_int),
+            "ldpm_set_bc": ([P, P, P, D], C.c_int),
+            "ldpm_info": ([P, P, P], C.c_int),
+            "ldpm_profile": ([P, I32], C.c_int),
+            "ldpm_profile_read": ([P, P, P, I32], C.c_int),
+            "ldpm_checkpoint_size": ([P], I64),
+            "ldpm_save_checkpoint": ([P, P], C.c_int),
+            "ldpm_load_checkpoint": ([P, P], C.c_int),
+            "ldpm_destroy": ([P], None),
+            "ldpm_last_error": ([], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != LDPM_OK:
+        raise LdpmError(rc, where, lib().ldpm_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None  # torch.cuda.Stream
+
+
+# --------------------------------------------------------------------------------------------------
+# Entry points with the C names.
+# --------------------------------------------------------------------------------------------------
+def ldpm_create(spec, material: dict, precision: int = LDPM_MIXED, dt: float = 0.0, dt_factor: float = 0.9,
+                bc=None, f_ext=None, stream=None, graph_chunk: int = 0, mass=None, inertia=None,
+                device: int = -1):
+    """Create a handle from a specimen (see specimen.Specimen) and a material dict.  Returns (handle,
+    keepalive) -- the caller-owned arrays only need to live for the duration of the call."""
+    keep = []
+
+    def arr(a, dtp):
+        if a is None:
+            return None
+        a = np.ascontiguousarray(a, dtype=dtp)
+        keep.append(a)
+        return a
+
+    g = Geometry(spec.n_particles, spec.n_tets, spec.n_facets, _ptr(arr(spec.x, np.float64)),
+                 _ptr(arr(spec.diameter, np.float64)), _ptr(arr(spec.tets, np.int32)),
+                 _ptr(arr(spec.facet_pi, np.int32)), _ptr(arr(spec.facet_pj, np.int32)),
+                 _ptr(arr(spec.facet_tet, np.int32)), _ptr(arr(spec.facet_vtx, np.float64)),
+                 _ptr(arr(mass, np.float64)), _ptr(arr(inertia, np.float64)))
+    m = Material(*[float(material[f]) for f in MATERIAL_FIELDS], int(material.get("elastic", 0)), 0)
+    o = Options()
+    o.precision = int(precision)
+    o.graph_chunk = int(graph_chunk)
+    o.dt = float(dt)
+    o.dt_factor = float(dt_factor)
+    o.cuda_stream = _stream_handle(stream)
+    o.device = int(device)
+    if bc is not None:
+        o.bc_mask = _ptr(arr(bc.mask, np.int32))
+        o.bc_vel = _ptr(arr(bc.vel, np.float64))
+        o.ramp_time = float(bc.ramp_time)
+        o.v0 = _ptr(arr(bc.v0, np.float64))
+    o.f_ext = _ptr(arr(f_ext, np.float64))
+    h = C.c_void_p()
+    _check(lib().ldpm_create(C.byref(g), C.byref(m), C.byref(o), C.byref(h)), "ldpm_create")
+    return h
+
+
+def ldpm_step(h, nsteps: int) -> None:
+    _check(lib().ldpm_step(h, int(nsteps)), "ldpm_step")
+
+
+def ldpm_sync(h) -> None:
+    _check(lib().ldpm_sync(h), "ldpm_sync")
+
+
+def ldpm_get_state(h, N: int, F: int, hist: bool = True):
+    q = np.zeros((N, 6))
+    v = np.zeros((N, 6))
+    h5 = np.zeros((F, 5)) if hist else None
+    st = C.c_int64(0)
+    _check(lib().ldpm_get_state(h, _ptr(q), _ptr(v), _ptr(h5), C.byref(st)), "ldpm_get_state")
+    return q, v, h5, st.value
+
+
+def ldpm_set_state(h, q, v, hist5=None, step: int = 0) -> None:
+    q = np.ascontiguousarray(q, np.float64)
+    v = np.ascontiguousarray(v, np.float64)
+    h5 = None if hist5 is None else np.ascontiguousarray(hist5, np.float64)
+    _check(lib().ldpm_set_state(h, _ptr(q), _ptr(v), _ptr(h5), int(step)), "ldpm_set_state")
+
+
+def ldpm_energy(h):
+    out = np.zeros(4)
+    r = np.zeros(12)
+    _check(lib().ldpm_energy(h, _ptr(out), _ptr(r)), "ldpm_energy")
+    return out, r
+
+
+def ldpm_facet_forces(h, N: int, F: int):
+    F3 = np.zeros((F, 3))
+    f6 = np.zeros((N, 6))
+    _check(lib().ldpm_facet_forces(h, _ptr(F3), _ptr(f6)), "ldpm_facet_forces")
+    return F3, f6
+
+
+def ldpm_set_bc(h, mask, vel, ramp_time: float) -> None:
+    mask = np.ascontiguousarray(mask, np.int32)
+    vel = None if vel is None else np.ascontiguousarray(vel, np.float64)
+    _check(lib().ldpm_set_bc(h, _ptr(mask), _ptr(vel), float(ramp_time)), "ldpm_set_bc")
+
+
+def ldpm_info(h):
+    info = np.zeros(5, np.int64)
+    dt = C.c_double(0.0)
+    _check(lib().ldpm_info(h, _ptr(info), C.byref(dt)), "ldpm_info")
+    return info, dt.value
+
+
+def ldpm_profile(h, enable: bool) -> None:
+    _check(lib().ldpm_profile(h, 1 if enable else 0), "ldpm_profile")
+
+
+def ldpm_profile_read(h):
+    ms = np.zeros(3)
+    cnt = np.zeros(3, np.int64)
+    _check(lib().ldpm_profile_read(h, _ptr(ms), _ptr(cnt), 3), "ldpm_profile_read")
+    return ms, cnt
+
+
+def ldpm_checkpoint_size(h) -> int:
+    n = lib().ldpm_checkpoint_size(h)
+    if n < 0:
+        _check(int(n), "ldpm_checkpoint_size")
+    return int(n)
+
+
+def ldpm_save_checkpoint(h) -> np.ndarray:
+    buf = np.zeros(ldpm_checkpoint_size(h), np.uint8)
+    _check(lib().ldpm_save_checkpoint(h, _ptr(buf)), "ldpm_save_checkpoint")
+    return buf
+
+
+def ldpm_load_checkpoint(h, buf) -> None:
+    buf = np.ascontiguousarray(buf, np.uint8)
+    _check(lib().ldpm_load_checkpoint(h, _ptr(buf)), "ldpm_load_checkpoint")
+
+
+def ldpm_destroy(h) -> None:
+    if h:
+        lib().ldpm_destroy(h)
+
+
+def ldpm_last_error() -> str:
+    return lib().ldpm_last_error().decode()
+
+
+# --------------------------------------------------------------------------------------------------
+# Convenience object (still marshalling only).
+# --------------------------------------------------------------------------------------------------
+class Model:
+    """One specimen on the GPU.  Arrays are in the specimen's own particle/facet order."""
+
+    def __init__(self, spec, material: dict, precision: str | int = "mixed", dt: float = 0.0, bc=None, **kw):
+        prec = precision if isinstance(precision, int) else (LDPM_MIXED if precision == "mixed" else LDPM_FP64)
+        self.N, self.T, self.F = spec.n_particles, spec.n_tets, spec.n_facets
+        self.h = ldpm_create(spec, material, prec, dt=dt, bc=bc, **kw)
+        info, self.dt = ldpm_info(self.h)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "h", None):
+            ldpm_destroy(self.h)
+            self.h = None
+
+    def step(self, n: int = 1):
+        ldpm_step(self.h, n)
+
+    def sync(self):
+        ldpm_sync(self.h)
+
+    def get_state(self, hist: bool = True):
+        return ldpm_get_state(self.h, self.N, self.F, hist)
+
+    def set_state(self, q, v, hist5=None, step: int = 0):
+        ldpm_set_state(self.h, q, v, hist5, step)
+
+    def energy(self):
+        return ldpm_energy(self.h)
+
+    def facet_forces(self):
+        return ldpm_facet_forces(self.h, self.N, self.F)
+
+    def set_bc(self, mask, vel, ramp_time):
+        ldpm_set_bc(self.h, mask, vel, ramp_time)
+
+    def info(self):
+        return ldpm_info(self.h)

@@ -1,0 +1,112 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol include/ldpm.h declares, and rejects
+bad input on the host before touching CUDA."""
+import dataclasses
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2603_13190_gb300 import ldpm, specimen, workloads
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(ldpm_[a-z0-9_]+)\s*\(", src, re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("ldpm_create", "ldpm_step", "ldpm_get_state", "ldpm_set_state", "ldpm_energy",
+                     "ldpm_facet_forces", "ldpm_destroy", "ldpm_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    L = ldpm.lib()
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def _expect(code, fn):
+    with pytest.raises(ldpm.LdpmError) as ei:
+        fn()
+    assert ei.value.code == code, str(ei.value)
+    return str(ei.value)
+
+
+@pytest.fixture(scope="module")
+def tet():
+    return specimen.single_tet_specimen()
+
+
+MAT = workloads.WORKLOAD_MATERIAL
+
+
+def test_rejects_facet_not_on_its_tetrahedron(tet):
+    bad = dataclasses.replace(tet, facet_pj=tet.facet_pi.copy())
+    _expect(-2, lambda: ldpm.ldpm_create(bad, MAT))
+
+
+def test_rejects_wrong_facet_count(tet):
+    bad = dataclasses.replace(tet, facet_pi=tet.facet_pi[:11], facet_pj=tet.facet_pj[:11],
+                              facet_tet=tet.facet_tet[:11], facet_vtx=tet.facet_vtx[:11])
+    _expect(-2, lambda: ldpm.ldpm_create(bad, MAT))
+
+
+def test_rejects_three_facets_on_one_edge(tet):
+    fpi, fpj = tet.facet_pi.copy(), tet.facet_pj.copy()
+    fpi[2], fpj[2] = fpi[0], fpj[0]
+    bad = dataclasses.replace(tet, facet_pi=fpi, facet_pj=fpj)
+    _expect(-2, lambda: ldpm.ldpm_create(bad, MAT))
+
+
+def test_rejects_flat_tetrahedron(tet):
+    x = tet.x.copy()
+    x[:, 2] = 0.0  # all four vertices in one plane
+    _expect(-2, lambda: ldpm.ldpm_create(dataclasses.replace(tet, x=x), MAT))
+
+
+def test_rejects_out_of_range_index(tet):
+    tets = tet.tets.copy()
+    tets[0, 0] = 99
+    _expect(-2, lambda: ldpm.ldpm_create(dataclasses.replace(tet, tets=tets), MAT))
+
+
+def test_rejects_edge_longer_than_l_t(tet):
+    _expect(-2, lambda: ldpm.ldpm_create(tet, dict(MAT, l_t=0.5)))
+
+
+@pytest.mark.parametrize("field,value,code", [("k_t", 0.5, -7), ("r_s", 0.1, -7), ("Ed_E0", 2.0, -7),
+                                              ("E0", -1.0, -1), ("alpha", float("nan"), -1)])
+def test_rejects_unsupported_or_invalid_material(tet, field, value, code):
+    _expect(code, lambda: ldpm.ldpm_create(tet, dict(MAT, **{field: value})))
+
+
+def test_rejects_bad_bc_code(tet):
+    bc = workloads.free_bc(4)
+    bc.mask[0, 0] = 7
+    _expect(-1, lambda: ldpm.ldpm_create(tet, MAT, bc=bc))
+
+
+def test_null_handle_calls_fail_cleanly():
+    L = ldpm.lib()
+    assert L.ldpm_step(None, 1) == -1
+    assert L.ldpm_energy(None, None, None) == -1
+    assert L.ldpm_sync(None) == -1
+    L.ldpm_destroy(None)
+    assert ldpm.ldpm_last_error() != ""
+
+
+def test_no_cpu_fallback_in_product_path():
+    """The binding and package never import the oracle."""
+    for fn in ("ldpm.py", "__init__.py", "build.py", "specimen.py", "workloads.py"):
+        src = open(os.path.join(ROOT, "paper_2603_13190_gb300", fn)).read()
+        assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), fn

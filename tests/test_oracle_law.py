@@ -195,3 +195,12 @@ def test_friction_cap_and_initial_slope_mu0():
     tN2, c2 = plateau(-2e-3)  # deep compression (elastic: -t_N < sigma_c0)
     sN0, mu0 = MAT["sigma_N0"], MAT["mu0"]
     assert abs(c2 - (ss + mu0 * sN0 * (1 - math.exp(tN2 / sN0)))) < 1e-9 * c2
+
+
+@pytest.mark.parametrize("eN", [1e-160, 1e-200, 5e-324])
+def test_vanishing_tensile_strain_is_elastic_not_nan(eN):
+    """At e_N > 0 so small that its square underflows, t / e is 0/0; the law's elastic limit t = E e
+    must come out (a loading wave leaves such strains ahead of its front)."""
+    e = np.array([eN, 0.0, 0.0])
+    t, em = oracle.facet_law(MAT, L_EDGE, e, e, 0.0, np.zeros(3), 0.0)
+    assert np.all(np.isfinite(t)) and t[0] == MAT["E0"] * eN and em >= 0.0
