@@ -180,6 +180,23 @@ int64_t ldpm_checkpoint_size(ldpm_t h);
 int ldpm_save_checkpoint(ldpm_t h, void *buf);
 int ldpm_load_checkpoint(ldpm_t h, const void *buf);
 
+/* Kinetic energy W_kin = sum_i 1/2 mass[i] v[i]^2 of caller-provided DEVICE arrays, written to the
+ * caller's DEVICE double *out, enqueued on `stream` (cudaStream_t; NULL = the legacy default stream)
+ * and returned without waiting.  The paper has no counterpart: this is a library service for callers
+ * that may not allocate device memory, such as code running inside another component's CUDA graph
+ * capture (where cudaMalloc is not permitted), processes whose device memory is owned by a fixed
+ * pool or caching allocator, and monitoring hooks that must not add the implicit synchronisation of
+ * an allocation to a running simulation.  It allocates nothing: its scratch (one partial sum per
+ * block of 1024 DOFs) is a 32 KiB static device array that every GPU loading the library holds until
+ * exit, so n_dof is limited to 4,194,304 (LDPM_E_INVALID_ARG beyond it, nothing launched).  The first
+ * call on a device looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current; make that first call before any stream capture.  All calls share the one array: every
+ * call overwrites the partials it reads, so nothing needs clearing, but calls that overlap on the GPU
+ * (on different streams, or from different threads) race on it and must be serialised by the
+ * caller.  The result equals the W_kin of ldpm_energy for the same velocities and masses up to
+ * summation order.  Errors: INVALID_ARG (NULL pointer, n_dof < 0, n_dof over the limit), CUDA. */
+int ldpm_kinetic_energy_noalloc(const double *v, const double *mass, int64_t n_dof, double *out, void *stream);
+
 /* Release everything the handle owns (synchronises first).  NULL is a no-op. */
 void ldpm_destroy(ldpm_t h);
 

@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libldpm.so")
-SOURCES = ("ldpm_kernels.cu", "ldpm_api.cu")
+SOURCES = ("ldpm_kernels.cu", "ldpm_api.cu", "ldpm_noalloc.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

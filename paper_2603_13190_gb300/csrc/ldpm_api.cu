@@ -25,8 +25,12 @@
 using namespace ldpm;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+void ldpm::set_last_error(const char *msg) { g_err = msg ? msg : ""; }
+
+namespace {
 
 int fail(int code, const char *fmt, ...)
 {

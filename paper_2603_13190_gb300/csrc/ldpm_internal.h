@@ -73,6 +73,9 @@ struct DeviceModel {
     int32_t *flag = nullptr;        // non-finite state seen
 };
 
+// Message returned by ldpm_last_error() on the calling thread (ldpm_api.cu).
+void set_last_error(const char *msg);
+
 // Launchers (ldpm_kernels.cu).  All enqueue on `s` and return the launch error.
 cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s);
 template <class R>

@@ -84,6 +84,7 @@ def lib():
             "ldpm_load_checkpoint": ([P, P], C.c_int),
             "ldpm_destroy": ([P], None),
             "ldpm_last_error": ([], C.c_char_p),
+            "ldpm_kinetic_energy_noalloc": ([P, P, I64, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -234,6 +235,13 @@ def ldpm_load_checkpoint(h, buf) -> None:
 def ldpm_destroy(h) -> None:
     if h:
         lib().ldpm_destroy(h)
+
+
+def ldpm_kinetic_energy_noalloc(v_dev: int, mass_dev: int, n_dof: int, out_dev: int, stream=None) -> None:
+    """Device pointers in, device pointer out; enqueued on `stream`, allocates nothing."""
+    _check(lib().ldpm_kinetic_energy_noalloc(C.c_void_p(v_dev), C.c_void_p(mass_dev), int(n_dof),
+                                             C.c_void_p(out_dev), _stream_handle(stream)),
+           "ldpm_kinetic_energy_noalloc")
 
 
 def ldpm_last_error() -> str:
