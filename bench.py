@@ -353,7 +353,20 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="uniaxial_tension")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ncu-case", choices=("mixed", "fp64"), default=None,
+                    help="profiling target: create the workload (dt = 2e-7 s, no estimate), run 4 steps "
+                         "with plain launches and exit; nothing is timed")
     args = ap.parse_args()
+    if args.ncu_case:
+        from paper_2603_13190_gb300 import ldpm
+
+        wl, spec, bc = make_inputs(args.workload)
+        m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=2e-7, bc=bc, graph_chunk=-1)
+        m.step(4)
+        m.sync()
+        m.close()
+        print("ncu case done: F=%d" % spec.n_facets)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

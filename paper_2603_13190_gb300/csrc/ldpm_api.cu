@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -159,7 +160,8 @@ void free_model(ldpm_ctx *h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.bc_vel, h->dm.f_ext, h->dm.tet, h->dm.geo,
+    void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.pm32, h->dm.bc_vel, h->dm.f_ext, h->dm.tet,
+                    h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
                     h->dm.step, h->dm.flag, h->d_partial, h->d_out16};
     for (void *p : ptrs)
@@ -450,7 +452,7 @@ int update_law(ldpm_ctx *h)
     return LDPM_OK;
 }
 
-int launch_facet_any(ldpm_ctx *h, int mode, const double *pst)
+int launch_facet_any(ldpm_ctx *h, int mode, const void *pst)
 {
     cudaError_t e = h->prec == LDPM_MIXED ? launch_facet<float>(h->dm, mode, pst, h->stream)
                                           : launch_facet<double>(h->dm, mode, pst, h->stream);
@@ -492,14 +494,27 @@ int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
     const int32_t N = h->dm.N;
     const size_t n6 = 6 * (size_t)N;
     int rc;
-    double *pst = nullptr, *out6 = nullptr;
-    if ((rc = dalloc(&pst, 16 * (size_t)N)) || (rc = dalloc(&out6, n6))) {
+    const bool mixed = h->prec == LDPM_MIXED;
+    const size_t rec = mixed ? (size_t)kMirror * sizeof(float) : 16 * sizeof(double);
+    void *pst = nullptr;
+    double *out6 = nullptr;
+    if ((rc = dalloc((char **)&pst, rec * (size_t)N)) || (rc = dalloc(&out6, n6))) {
         cudaFree(pst);
         return rc;
     }
+    // displacement x (iteration vector) on the reference positions; zero velocity
     std::vector<double> ps(16 * (size_t)N, 0.0), x(n6), f(n6);
+    std::vector<float> pm(mixed ? (size_t)kMirror * N : 0, 0.0f);
     for (int32_t p = 0; p < N; ++p)
-        for (int a = 0; a < 3; ++a) ps[16 * (size_t)p + a] = h->x_int[3 * (size_t)p + a];
+        for (int a = 0; a < 3; ++a) {
+            const double xv = h->x_int[3 * (size_t)p + a];
+            ps[16 * (size_t)p + a] = xv;
+            if (mixed) {
+                const float hi = (float)xv;
+                pm[kMirror * (size_t)p + a] = hi;
+                pm[kMirror * (size_t)p + 3 + a] = (float)(xv - (double)hi);
+            }
+        }
     std::mt19937_64 rng(12345);
     std::normal_distribution<double> nd;
     for (auto &v : x) v = nd(rng);
@@ -516,8 +531,24 @@ int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
             for (size_t i = a; i < b; ++i) x[i] /= nrm;
         }
         for (int32_t p = 0; p < N; ++p)
-            for (int k = 0; k < 6; ++k) ps[16 * (size_t)p + 3 + k] = x[6 * (size_t)p + k];
-        CU(cudaMemcpyAsync(pst, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+            for (int k = 0; k < 6; ++k) {
+                const double u = x[6 * (size_t)p + k];
+                ps[16 * (size_t)p + 3 + k] = u;
+                if (mixed) {
+                    float *r = &pm[kMirror * (size_t)p];
+                    if (k < 3) {
+                        const float hi = (float)u;
+                        r[6 + k] = hi;
+                        r[9 + k] = (float)(u - (double)hi);
+                    } else {
+                        r[12 + k - 3] = (float)u;
+                    }
+                }
+            }
+        if (mixed)
+            CU(cudaMemcpyAsync(pst, pm.data(), pm.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+        else
+            CU(cudaMemcpyAsync(pst, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
         if ((rc = launch_facet_any(h, FACET_ELASTIC, pst)) || (rc = launch_gather_any(h, GATHER_ASSEMBLE, out6))) break;
         CU(cudaMemcpyAsync(f.data(), out6, n6 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CU(cudaStreamSynchronize(h->stream));
@@ -653,7 +684,17 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     dm.N = N;
     dm.T = T;
     dm.n_spec = n;
-    dm.tets_per_block = kTile;
+    dm.tets_per_block = 8;  // measured fastest of 8/16/32 on GB300 (uniaxial_tension, mixed)
+    dm.gather_lanes = 8;    // measured fastest of 8/16/32
+    // Launch-shape overrides for tuning: LDPM_GATHER_LANES (8, 16, 32), LDPM_TETS_PER_BLOCK (8, 16, 32).
+    if (const char *ev = std::getenv("LDPM_GATHER_LANES")) {
+        const int v = std::atoi(ev);
+        if (v == 8 || v == 16 || v == 32) dm.gather_lanes = v;
+    }
+    if (const char *ev = std::getenv("LDPM_TETS_PER_BLOCK")) {
+        const int v = std::atoi(ev);
+        if (v == 8 || v == 16 || v == 32) dm.tets_per_block = v;
+    }
     int rc;
     if ((rc = dalloc(&dm.pstate, 16 * (size_t)N)) || (rc = dalloc(&dm.pdyn, 8 * (size_t)N)) ||
         (rc = dalloc(&dm.pconst, 8 * (size_t)N)) || (rc = dalloc(&dm.bc_vel, 6 * (size_t)N)) ||
@@ -666,6 +707,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         if ((rc = dalloc(&dm.f_ext, 6 * (size_t)N))) return rc;
         CU(cudaMemcpy(dm.f_ext, H.f_ext.data(), H.f_ext.size() * sizeof(double), cudaMemcpyHostToDevice));
     }
+    if (h->prec == LDPM_MIXED && (rc = dalloc(&dm.pm32, (size_t)kMirror * N))) return rc;
     CU(cudaMallocHost((void **)&h->h_out16, 16 * sizeof(double)));
     CU(cudaMemcpy(dm.pstate, H.pstate.data(), H.pstate.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.pdyn, H.pdyn.data(), H.pdyn.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -676,6 +718,8 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     CU(cudaMemcpy(dm.tile_spec, H.tile_spec.data(), H.tile_spec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CU(cudaMemset(dm.step, 0, sizeof(int64_t)));
     CU(cudaMemset(dm.flag, 0, sizeof(int32_t)));
+    CU(launch_mirror(dm, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     for (auto &S : h->sp)
         if (!(S.dt > 0)) S.dt = 1.0;  // placeholder until estimated
     if (h->prec == LDPM_MIXED)
@@ -972,6 +1016,7 @@ int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *his
             base_f += S.F;
         }
         CU(cudaMemcpy(h->dm.pstate, ps.data(), ps.size() * sizeof(double), cudaMemcpyHostToDevice));
+        CU(launch_mirror(h->dm, h->stream));
         CU(cudaMemset(h->dm.pdyn, 0, 8 * (size_t)h->dm.N * sizeof(double)));
         double *d5 = nullptr;
         if ((rc = dalloc(&d5, 5 * (size_t)Fint))) return rc;
@@ -1191,6 +1236,8 @@ int ldpm_load_checkpoint(ldpm_t h, const void *buf)
     int32_t fl = (int32_t)fl64;
     CU(cudaMemcpy(h->dm.flag, &fl, 4, cudaMemcpyHostToDevice));
     for (size_t s = 0; s < h->sp.size(); ++s) std::memcpy(&h->sp[s].W_kin0, q + 16 + 8 * s, 8);
+    CU(launch_mirror(h->dm, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
     return LDPM_OK;
 }
 

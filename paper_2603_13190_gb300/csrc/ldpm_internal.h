@@ -6,6 +6,9 @@
 //   pstate [N][16] f64  x(3) q(6) v(6) pad      gathered by the facet pass (one 128-byte line)
 //   pdyn   [N][8]  f64  f_asm(6) W_int W_ext     node force sums of the current step, energy sums
 //   pconst [N][8]  f64  1/mass(6) bc-bits spec   per-DOF inverse mass, 8-bit BC code per DOF, specimen
+//   pm32   [N][24] f32  mixed mode only: FP32 mirror read by the facet pass, written by the particle
+//                       kernels: x_hi(3) x_lo(3) u_hi(3) u_lo(3) theta(3) v(3) omega(3) pad(3), where
+//                       hi = float(a), lo = float(a - hi) (a two-float split of an FP64 value)
 //   tet    [T]     int4 particle ids of the 4 vertices (-1: padding tetrahedron)
 //   geo    [12T]   R4   c_a (arm from the edge's first vertex to the facet centroid), projected area A
 //   hist   [12T]   R4   t_N, t_M, t_L, e_max
@@ -20,6 +23,8 @@
 #include <cuda_runtime.h>
 
 namespace ldpm {
+
+constexpr int kMirror = 24;  // floats per particle in the FP32 mirror
 
 struct alignas(32) double4a {
     double x, y, z, w;
@@ -62,6 +67,8 @@ struct DeviceModel {
     int32_t n_spec = 0;
     int32_t tets_per_block = 32;
     double *pstate = nullptr, *pdyn = nullptr, *pconst = nullptr;
+    float *pm32 = nullptr;          // FP32 mirror (mixed mode), null in FP64 mode
+    int32_t gather_lanes = 8;       // lanes per particle in the particle pass (8, 16 or 32)
     double *bc_vel = nullptr, *f_ext = nullptr;
     int4 *tet = nullptr;
     void *geo = nullptr, *hist = nullptr, *fout = nullptr, *ent = nullptr;
@@ -78,8 +85,12 @@ void set_last_error(const char *msg);
 
 // Launchers (ldpm_kernels.cu).  All enqueue on `s` and return the launch error.
 cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s);
+// `src_override` replaces the particle records the facet pass reads (FP64 mode: pstate layout;
+// mixed mode: pm32 layout); null = the model's own.
 template <class R>
-cudaError_t launch_facet(const DeviceModel &m, int mode, const double *pstate_override, cudaStream_t s);
+cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s);
+// Rebuild the FP32 mirror from pstate (after create, set_state, checkpoint load).  No-op in FP64.
+cudaError_t launch_mirror(const DeviceModel &m, cudaStream_t s);
 template <class R>
 cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStream_t s);
 // Energy sums over particles [p0, p1): out16 = W_int, W_ext, W_kin, pad, reaction fixed(6),

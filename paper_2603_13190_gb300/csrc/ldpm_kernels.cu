@@ -152,16 +152,17 @@ __device__ __forceinline__ void facet_law(const LawConst<R> &c, R l, V3<R> e, V3
 
 // ------------------------------------------------------------------------------------------------
 // Facet pass.  A block owns TETS consecutive tetrahedra (12 * TETS facets, one thread each).
-// Phase A: 4 threads per tetrahedron gather the vertex records (x, q, v; one 128-byte line each),
-// form FP64 differences to vertex 0 of the tetrahedron, round them to R and park them in shared
-// memory, and compute the tetrahedron's volumetric strain.  Phase B: one thread per facet.
+// Phase A: 4 threads per tetrahedron gather the vertex records (FP64 mode: x, q, v, one 128-byte
+// line; mixed mode: the 96-byte FP32 mirror), form differences to vertex 0 of the tetrahedron in R,
+// park them in shared memory, and compute the tetrahedron's volumetric strain.  Phase B: one thread
+// per facet.
 // The facet's own geometry and history are loaded before phase A so their HBM latency overlaps
 // the gathers.
 // ------------------------------------------------------------------------------------------------
 constexpr int kVtx = 15;  // dx(3) du(3) dv(3) theta(3) omega(3)
 
 template <class R, int MODE, int TETS>
-__global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const double *__restrict__ pst)
+__global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const void *__restrict__ vsrc)
 {
     __shared__ R sv[TETS * 4][kVtx];  // odd row stride: conflict-free per-lane writes
     __shared__ R seV[TETS];
@@ -193,37 +194,69 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const d
         const int64_t tt = tet0 + jt;
         int p = -1;
         if (tt < m.T) p = reinterpret_cast<const int *>(m.tet)[4 * tt + vi];
-        double rec[15];
-        if (p >= 0) {
-            const double2 *r2 = reinterpret_cast<const double2 *>(pst + 16 * (int64_t)p);
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                const double2 w = r2[k];
-                rec[2 * k] = w.x;
-                rec[2 * k + 1] = w.y;
-            }
-            rec[14] = pst[16 * (int64_t)p + 14];
-        } else {
-#pragma unroll
-            for (int k = 0; k < 15; ++k) rec[k] = 0.0;
-        }
-        // rec: x 0..2, u 3..5, theta 6..8, v 9..11, omega 12..14
         const int base = (threadIdx.x & 31) & ~3;
-        double ref[9];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            ref[k] = __shfl_sync(0xffffffffu, rec[k], base);
-            ref[3 + k] = __shfl_sync(0xffffffffu, rec[3 + k], base);
-            ref[6 + k] = __shfl_sync(0xffffffffu, rec[9 + k], base);
-        }
         R *o = sv[tid];
+        if constexpr (sizeof(R) == 4) {
+            // Mixed mode: the FP32 mirror record (x, u as hi/lo float pairs; theta, v, omega).  A
+            // difference (a_hi - b_hi) + (a_lo - b_lo) carries FP32 relative accuracy of the
+            // difference itself, so no FP64 instruction is needed here.
+            const float *src = static_cast<const float *>(vsrc);
+            float rec[24];
+            if (p >= 0) {
+                const float4 *r4 = reinterpret_cast<const float4 *>(src + kMirror * (int64_t)p);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            o[k] = R(rec[k] - ref[k]);              // dx
-            o[3 + k] = R(rec[3 + k] - ref[3 + k]);  // du
-            o[6 + k] = R(rec[9 + k] - ref[6 + k]);  // dv
-            o[9 + k] = R(rec[6 + k]);               // theta
-            o[12 + k] = R(rec[12 + k]);             // omega
+                for (int k = 0; k < 6; ++k) {
+                    const float4 w = r4[k];
+                    rec[4 * k] = w.x;
+                    rec[4 * k + 1] = w.y;
+                    rec[4 * k + 2] = w.z;
+                    rec[4 * k + 3] = w.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < 24; ++k) rec[k] = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const float x0h = __shfl_sync(0xffffffffu, rec[k], base);
+                const float x0l = __shfl_sync(0xffffffffu, rec[3 + k], base);
+                const float u0h = __shfl_sync(0xffffffffu, rec[6 + k], base);
+                const float u0l = __shfl_sync(0xffffffffu, rec[9 + k], base);
+                const float v0 = __shfl_sync(0xffffffffu, rec[15 + k], base);
+                o[k] = (rec[k] - x0h) + (rec[3 + k] - x0l);        // dx
+                o[3 + k] = (rec[6 + k] - u0h) + (rec[9 + k] - u0l);  // du
+                o[6 + k] = rec[15 + k] - v0;                        // dv
+                o[9 + k] = rec[12 + k];                             // theta
+                o[12 + k] = rec[18 + k];                            // omega
+            }
+        } else {
+            // FP64 mode: the FP64 record x(3) u(3) theta(3) v(3) omega(3).
+            const double *src = static_cast<const double *>(vsrc);
+            double rec[15];
+            if (p >= 0) {
+                const double2 *r2 = reinterpret_cast<const double2 *>(src + 16 * (int64_t)p);
+#pragma unroll
+                for (int k = 0; k < 7; ++k) {
+                    const double2 w = r2[k];
+                    rec[2 * k] = w.x;
+                    rec[2 * k + 1] = w.y;
+                }
+                rec[14] = src[16 * (int64_t)p + 14];
+            } else {
+#pragma unroll
+                for (int k = 0; k < 15; ++k) rec[k] = 0.0;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const double x0 = __shfl_sync(0xffffffffu, rec[k], base);
+                const double u0 = __shfl_sync(0xffffffffu, rec[3 + k], base);
+                const double v0 = __shfl_sync(0xffffffffu, rec[9 + k], base);
+                o[k] = R(rec[k] - x0);
+                o[3 + k] = R(rec[3 + k] - u0);
+                o[6 + k] = R(rec[9 + k] - v0);
+                o[9 + k] = R(rec[6 + k]);
+                o[12 + k] = R(rec[12 + k]);
+            }
         }
         // e_V = (1/3) div u of the linear tetrahedron.  With D = [dx1 dx2 dx3], grad N_i (i = 1..3)
         // are the rows of D^-1 = [dx2 x dx3; dx3 x dx1; dx1 x dx2] / det D, and vertex 0 carries no
@@ -268,7 +301,7 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const d
     const V3<R> ca = {g.x, g.y, g.z};
     const V3<R> cb = ca - d;
     R tN, tM, tL, emax;
-    const int sp = m.tile_spec ? m.tile_spec[blockIdx.x] : 0;
+    const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;  // specimens are padded to 32 tetrahedra
     const LawConst<R> &c = lawc[sp];
     if (MODE == FACET_FROM_HIST) {
         tN = h.x;
@@ -312,8 +345,13 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const d
 }
 
 // ------------------------------------------------------------------------------------------------
-// Particle pass: one warp per particle sums its facet ends in CSR order (Eq. (2a)-(2b)), then
-// lanes 0..5 update one DOF each.
+// Particle pass.  A group of LPP lanes owns one particle: it sums the particle's facet ends in CSR
+// order (Eq. (2a)-(2b)), reduces across the group, and lanes 0..5 of the group update one DOF each.
+// In mixed mode the facet forces are FP32 values and their sums are formed in FP32 (this adds
+// rounding of the same order as the forces' own); everything after the sum is FP64.  With LPP = 8 a
+// warp updates 4 particles per FP64 instruction: the GB300 FP64 pipe issues one warp instruction
+// per ~64 cycles per sub-partition, so FP64 instruction count, not bytes, bounds this pass if the
+// whole warp serves one particle.
 // ------------------------------------------------------------------------------------------------
 __device__ __forceinline__ double ramp(double t, double T)
 {
@@ -325,94 +363,128 @@ __device__ __forceinline__ double ramp(double t, double T)
 __device__ __forceinline__ int entry_bits(float w) { return __float_as_int(w); }
 __device__ __forceinline__ int64_t entry_bits(double w) { return __double_as_longlong(w); }
 
-template <class R, int MODE>
+// Finite test on the exponent bits (integer pipe).
+__device__ __forceinline__ bool finite_bits(double x)
+{
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// FP32 mirror entries of DOF d of particle p after its FP64 q and v changed.
+__device__ __forceinline__ void write_mirror(float *pm, int d, double q, double v)
+{
+    if (d < 3) {
+        const float hi = float(q);
+        pm[6 + d] = hi;
+        pm[9 + d] = float(q - double(hi));
+        pm[15 + d] = float(v);
+    } else {
+        pm[12 + d - 3] = float(q);
+        pm[18 + d - 3] = float(v);
+    }
+}
+
+template <class R, int MODE, int LPP>
 __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
+    static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per particle");
     using T4 = R4<R>;
     const T4 *__restrict__ ent = static_cast<const T4 *>(m.ent);
     const T4 *__restrict__ fout = static_cast<const T4 *>(m.fout);
     const int lane = threadIdx.x & 31;
-    const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (p >= m.N) return;
-    const int r0 = m.row[p], r1 = m.row[p + 1];
-    R a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0, a5 = 0;
-    for (int r = r0 + lane; r < r1; r += 32) {
-        const T4 en = ent[r];
-        const int64_t bits = entry_bits(en.w);
-        const T4 F = fout[bits >> 1];
-        const R sg = (bits & 1) ? R(-1) : R(1);
-        const V3<R> Fs = {sg * F.x, sg * F.y, sg * F.z};
-        const V3<R> mo = cross(V3<R>{en.x, en.y, en.z}, Fs);
-        a0 += Fs.x;
-        a1 += Fs.y;
-        a2 += Fs.z;
-        a3 += mo.x;
-        a4 += mo.y;
-        a5 += mo.z;
+    const int sub = lane & (LPP - 1);
+    const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
+    const bool valid = p < m.N;
+    int r0 = 0, r1 = 0;
+    if (valid) {
+        r0 = m.row[p];
+        r1 = m.row[p + 1];
     }
-    double s[6] = {double(a0), double(a1), double(a2), double(a3), double(a4), double(a5)};
+    R a[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    for (int r = r0 + sub; r < r1; r += 4 * LPP) {
+        T4 en[4], F[4];
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1)
+        for (int k = 0; k < 4; ++k)
+            if (r + k * LPP < r1) en[k] = ent[r + k * LPP];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) s[k] += __shfl_xor_sync(0xffffffffu, s[k], off);
-    // lanes 0..5 own one DOF each; the other lanes mirror DOF 0 and store nothing
-    const bool act = lane < 6;
-    double fa_new = s[0];
+        for (int k = 0; k < 4; ++k)
+            if (r + k * LPP < r1) F[k] = fout[entry_bits(en[k].w) >> 1];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (r + k * LPP < r1) {
+                const R sg = (entry_bits(en[k].w) & 1) ? R(-1) : R(1);
+                const V3<R> Fs = {sg * F[k].x, sg * F[k].y, sg * F[k].z};
+                const V3<R> mo = cross(V3<R>{en[k].x, en[k].y, en[k].z}, Fs);
+                a[0] += Fs.x;
+                a[1] += Fs.y;
+                a[2] += Fs.z;
+                a[3] += mo.x;
+                a[4] += mo.y;
+                a[5] += mo.z;
+            }
+    }
+#pragma unroll
+    for (int off = LPP / 2; off > 0; off >>= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+    // lanes 0..5 of the group own one DOF each; the other lanes mirror DOF 0 and store nothing
+    const bool act = valid && sub < 6;
+    const int d = sub < 6 ? sub : 0;
+    R fr = a[0];
 #pragma unroll
     for (int k = 1; k < 6; ++k)
-        if (lane == k) fa_new = s[k];
+        if (d == k) fr = a[k];
+    const double fa_new = double(fr);
     if (MODE == GATHER_ASSEMBLE) {
-        if (act) out6[6 * p + lane] = fa_new;
+        if (act) out6[6 * p + d] = fa_new;
         return;
     }
     // ---- velocity-form central difference for DOF d (state on entry: q_{n+1}, v_{n+1/2}, f_n)
-    const int d = act ? lane : 0;
-    double *ps = m.pstate + 16 * p;
-    double *pd = m.pdyn + 8 * p;
-    const double *pc = m.pconst + 8 * p;
+    const int64_t pc_ = valid ? p : 0;
+    double *ps = m.pstate + 16 * pc_;
+    double *pd = m.pdyn + 8 * pc_;
+    const double *pc = m.pconst + 8 * pc_;
     const double im = pc[d];
     const uint64_t bcbits = (uint64_t)__double_as_longlong(pc[6]);
     const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
     const int sp = (int)__double_as_longlong(pc[7]);
-    const double dt = m.spec[sp].dt, Tr = m.spec[sp].ramp_time;
-    const int64_t n1 = *m.step;
-    const double t1 = (double)n1 * dt;
-    const double t0 = (double)(n1 - 1) * dt;
-    const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
+    const double dt = m.spec[sp].dt;
+    const double fe = m.f_ext ? m.f_ext[6 * pc_ + d] : 0.0;
     const double vh = ps[9 + d];
     const double fa_old = pd[d];
-    const double dq = dt * vh;
-    double g_old, g_new, v_new, v_next;
+    double g_sum, v_new, v_next;
     if (mask == 0) {
-        g_old = fe;
-        g_new = fe;
-        const double a = (fe + fa_new) * im;
-        v_new = vh + 0.5 * dt * a;
-        v_next = v_new + 0.5 * dt * a;
+        const double a_ = (fe + fa_new) * im;
+        g_sum = 2.0 * fe;
+        v_new = vh + 0.5 * dt * a_;
+        v_next = v_new + 0.5 * dt * a_;
     } else if (mask == 1) {
-        g_old = -fa_old;
-        g_new = -fa_new;
+        g_sum = -(fa_old + fa_new);
         v_new = 0.0;
         v_next = 0.0;
     } else {
-        const double vb = m.bc_vel[6 * p + d];
+        const double Tr = m.spec[sp].ramp_time;
+        const int64_t n1 = *m.step;
+        const double t1 = (double)n1 * dt;
+        const double t0 = (double)(n1 - 1) * dt;
+        const double vb = m.bc_vel[6 * pc_ + d];
         const double mass = 1.0 / im;
         const double a_old = vb * (ramp(t0 + 0.5 * dt, Tr) - ramp(t0 - 0.5 * dt, Tr)) / dt;
         const double a_new = vb * (ramp(t1 + 0.5 * dt, Tr) - ramp(t1 - 0.5 * dt, Tr)) / dt;
-        g_old = mass * a_old - fa_old;
-        g_new = mass * a_new - fa_new;
+        g_sum = mass * (a_old + a_new) - (fa_old + fa_new);
         v_new = vb * ramp(t1, Tr);
         v_next = vb * ramp(t1 + 0.5 * dt, Tr);
     }
-    double dWe = act ? 0.5 * (g_old + g_new) * dq : 0.0;
-    double dWi = act ? 0.5 * (-fa_old - fa_new) * dq : 0.0;
+    // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
+    const double hdq = 0.5 * dt * vh;
+    double dWe = act ? g_sum * hdq : 0.0;
+    double dWi = act ? -(fa_old + fa_new) * hdq : 0.0;
     double q = ps[3 + d];
     double v_store = v_new;
     if (MODE != GATHER_STEP_LAST) {
         v_store = v_next;
         q += dt * v_next;
     }
-    // sum the six DOF contributions into lane 0 (lanes 6, 7 hold zeros)
+    // sum the six DOF contributions into lane 0 of the group (lanes 6, 7 hold zeros)
 #pragma unroll
     for (int off = 4; off > 0; off >>= 1) {
         dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
@@ -422,11 +494,12 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
         pd[d] = fa_new;
         if (MODE != GATHER_STEP_LAST) ps[3 + d] = q;
         ps[9 + d] = v_store;
-        if (!isfinite(v_store) || !isfinite(q)) *(volatile int32_t *)m.flag = 1;
-    }
-    if (lane == 0) {
-        pd[6] += dWi;
-        pd[7] += dWe;
+        if (m.pm32) write_mirror(m.pm32 + kMirror * pc_, d, q, v_store);
+        if (!finite_bits(v_store) || !finite_bits(q)) *(volatile int32_t *)m.flag = 1;
+        if (sub == 0) {
+            pd[6] += dWi;
+            pd[7] += dWe;
+        }
     }
 }
 
@@ -442,7 +515,6 @@ __global__ void __launch_bounds__(256) kick_kernel(DeviceModel m)
     const int mask = (int)(((uint64_t)__double_as_longlong(pc[6]) >> (8 * d)) & 0xffu);
     const int sp = (int)__double_as_longlong(pc[7]);
     const double dt = m.spec[sp].dt;
-    const double t = (double)(*m.step) * dt;
     double vh;
     if (mask == 0) {
         const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
@@ -450,10 +522,29 @@ __global__ void __launch_bounds__(256) kick_kernel(DeviceModel m)
     } else if (mask == 1) {
         vh = 0.0;
     } else {
+        const double t = (double)(*m.step) * dt;
         vh = m.bc_vel[6 * p + d] * ramp(t + 0.5 * dt, m.spec[sp].ramp_time);
     }
+    const double q = ps[3 + d] + dt * vh;
     ps[9 + d] = vh;
-    ps[3 + d] += dt * vh;
+    ps[3 + d] = q;
+    if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, q, vh);
+}
+
+// FP32 mirror of every particle from the FP64 records.
+__global__ void __launch_bounds__(256) mirror_kernel(DeviceModel m)
+{
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= m.N) return;
+    const double *ps = m.pstate + 16 * p;
+    float *pm = m.pm32 + kMirror * p;
+    for (int k = 0; k < 3; ++k) {
+        const float hi = float(ps[k]);
+        pm[k] = hi;
+        pm[3 + k] = float(ps[k] - double(hi));
+    }
+    for (int d = 0; d < 6; ++d) write_mirror(pm, d, ps[3 + d], ps[9 + d]);
+    for (int k = 21; k < kMirror; ++k) pm[k] = 0.0f;
 }
 
 // Energy sums over particles [p0, p1) (per block, fixed order), then one block adds the partials.
@@ -535,10 +626,20 @@ __device__ __forceinline__ bool facet_frame_of(const DeviceModel &m, int64_t f, 
     const int *tv = reinterpret_cast<const int *>(m.tet) + 4 * tt;
     const int p0 = tv[0], pa = tv[va], pb = tv[vb];
     if (p0 < 0) return false;
-    const double *x0 = m.pstate + 16 * (int64_t)p0, *xa = m.pstate + 16 * (int64_t)pa,
-                 *xb = m.pstate + 16 * (int64_t)pb;
-    const V3<R> dxa = {R(xa[0] - x0[0]), R(xa[1] - x0[1]), R(xa[2] - x0[2])};
-    const V3<R> dxb = {R(xb[0] - x0[0]), R(xb[1] - x0[1]), R(xb[2] - x0[2])};
+    V3<R> dxa, dxb;
+    if constexpr (sizeof(R) == 4) {
+        const float *x0 = m.pm32 + kMirror * (int64_t)p0, *xa = m.pm32 + kMirror * (int64_t)pa,
+                    *xb = m.pm32 + kMirror * (int64_t)pb;
+        dxa = {(xa[0] - x0[0]) + (xa[3] - x0[3]), (xa[1] - x0[1]) + (xa[4] - x0[4]),
+               (xa[2] - x0[2]) + (xa[5] - x0[5])};
+        dxb = {(xb[0] - x0[0]) + (xb[3] - x0[3]), (xb[1] - x0[1]) + (xb[4] - x0[4]),
+               (xb[2] - x0[2]) + (xb[5] - x0[5])};
+    } else {
+        const double *x0 = m.pstate + 16 * (int64_t)p0, *xa = m.pstate + 16 * (int64_t)pa,
+                     *xb = m.pstate + 16 * (int64_t)pb;
+        dxa = {R(xa[0] - x0[0]), R(xa[1] - x0[1]), R(xa[2] - x0[2])};
+        dxb = {R(xb[0] - x0[0]), R(xb[1] - x0[1]), R(xb[2] - x0[2])};
+    }
     const V3<R> d = dxb - dxa;
     const R inv_l = rsqrt_(dot(d, d));
     n = inv_l * d;
@@ -584,7 +685,7 @@ __global__ void hist_from_user_kernel(DeviceModel m, const double *__restrict__ 
 }
 
 template <class R, int MODE>
-cudaError_t launch_facet_tpb(const DeviceModel &m, const double *pst, cudaStream_t s)
+cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t s)
 {
     const int tpb = m.tets_per_block;
     const unsigned blocks = (unsigned)((m.T + tpb - 1) / tpb);
@@ -614,9 +715,11 @@ cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s)
 }
 
 template <class R>
-cudaError_t launch_facet(const DeviceModel &m, int mode, const double *pstate_override, cudaStream_t s)
+cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s)
 {
-    const double *pst = pstate_override ? pstate_override : m.pstate;
+    const void *pst = src_override ? src_override
+                                   : (sizeof(R) == 4 ? static_cast<const void *>(m.pm32)
+                                                     : static_cast<const void *>(m.pstate));
     switch (mode) {
     case FACET_FROM_HIST:
         return launch_facet_tpb<R, FACET_FROM_HIST>(m, pst, s);
@@ -627,23 +730,43 @@ cudaError_t launch_facet(const DeviceModel &m, int mode, const double *pstate_ov
     }
 }
 
+template <class R, int LPP>
+cudaError_t launch_gather_lpp(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
+{
+    const int64_t warps = ((int64_t)m.N + (32 / LPP) - 1) / (32 / LPP);
+    const unsigned blocks = (unsigned)((warps * 32 + 255) / 256);
+    switch (mode) {
+    case GATHER_ASSEMBLE:
+        gather_kernel<R, GATHER_ASSEMBLE, LPP><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    case GATHER_STEP_LAST:
+        gather_kernel<R, GATHER_STEP_LAST, LPP><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    default:
+        gather_kernel<R, GATHER_STEP_MID, LPP><<<blocks, 256, 0, s>>>(m, out6);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 template <class R>
 cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
 {
-    const int64_t threads = 32 * (int64_t)m.N;
-    if (threads == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((threads + 255) / 256);
-    switch (mode) {
-    case GATHER_ASSEMBLE:
-        gather_kernel<R, GATHER_ASSEMBLE><<<blocks, 256, 0, s>>>(m, out6);
-        break;
-    case GATHER_STEP_LAST:
-        gather_kernel<R, GATHER_STEP_LAST><<<blocks, 256, 0, s>>>(m, out6);
-        break;
+    if (m.N == 0) return cudaSuccess;
+    switch (m.gather_lanes) {
+    case 32:
+        return launch_gather_lpp<R, 32>(m, mode, out6, s);
+    case 16:
+        return launch_gather_lpp<R, 16>(m, mode, out6, s);
     default:
-        gather_kernel<R, GATHER_STEP_MID><<<blocks, 256, 0, s>>>(m, out6);
-        break;
+        return launch_gather_lpp<R, 8>(m, mode, out6, s);
     }
+}
+
+cudaError_t launch_mirror(const DeviceModel &m, cudaStream_t s)
+{
+    if (!m.pm32 || m.N == 0) return cudaSuccess;
+    mirror_kernel<<<(unsigned)((m.N + 255) / 256), 256, 0, s>>>(m);
     return cudaGetLastError();
 }
 
@@ -675,8 +798,8 @@ cudaError_t launch_hist_from_user(const DeviceModel &m, const double *in5, cudaS
     return cudaGetLastError();
 }
 
-template cudaError_t launch_facet<float>(const DeviceModel &, int, const double *, cudaStream_t);
-template cudaError_t launch_facet<double>(const DeviceModel &, int, const double *, cudaStream_t);
+template cudaError_t launch_facet<float>(const DeviceModel &, int, const void *, cudaStream_t);
+template cudaError_t launch_facet<double>(const DeviceModel &, int, const void *, cudaStream_t);
 template cudaError_t launch_gather<float>(const DeviceModel &, int, double *, cudaStream_t);
 template cudaError_t launch_gather<double>(const DeviceModel &, int, double *, cudaStream_t);
 template cudaError_t launch_hist_to_user<float>(const DeviceModel &, double *, cudaStream_t);
