@@ -31,17 +31,22 @@ sys.path.insert(0, ROOT)
 METRIC = "facet-updates/s per explicit step and % of HBM roofline, mixed vs FP64"
 UNIT = "facet-updates/s"
 
-# Algorithmic bytes per facet of the facet pass (values the method must read or write once per
-# step): geometry c_a + A, history read + write, facet force (3 values), tetrahedron ids / 12, and the
-# vertex records x, q, v (15 doubles) once per particle.
+# Algorithmic bytes of one facet-pass launch: values the method reads or writes once per step.
+#   per facet        geometry (arm c_I, area A) 4r, history read + written 8r
+#   per tetrahedron  4 particle ids 16 B, its 4 vertex force/moment shares written 24r
+#   per particle     the record the pass gathers once: mixed 21 floats (x, u as hi/lo pairs,
+#                    theta, v, omega) = 84 B; FP64 15 doubles (x, q, v) = 120 B
 def facet_pass_bytes(F: int, T: int, N: int, r: int) -> float:
-    return F * (4 * r + 8 * r + 3 * r) + T * 16 + N * 120
+    return F * 12 * r + T * (16 + 24 * r) + N * (84 if r == 4 else 120)
 
 
-def gather_pass_bytes(F: int, N: int, r: int) -> float:
-    # two facet ends per facet: arm (3 r) + id (r) and the facet force (3 r) each; per particle the
-    # row pointer, q and v read and written, forces and energy sums read and written, constants read.
-    return F * 2 * (4 * r + 3 * r) + N * (4 + 96 + 96 + 64 + 64 + 64)
+# Algorithmic bytes of one particle-pass launch.
+#   per tetrahedron  4 CSR slot ids (4 B) and the 4 shares read (24r)
+#   per particle     row pointer 4 B; q, v read and written 192 B; forces and energy sums read and
+#                    written 128 B; inverse masses, BC codes, specimen 64 B; mixed mode writes the
+#                    FP32 record 84 B
+def gather_pass_bytes(T: int, N: int, r: int) -> float:
+    return T * 4 * (4 + 6 * r) + N * (4 + 192 + 128 + 64 + (84 if r == 4 else 0))
 
 
 def kernel_src_hash() -> str:
@@ -222,7 +227,7 @@ def run_ours(args, rank, world, local):
         # per-kernel durations from events around each launch (same stream), separate pass
         _, kern = time_steps(model, ldpm, torch, stream, flush, steps, 1, profile=True)
         r = 4 if prec == "mixed" else 8
-        fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(F, N, r)
+        fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(T, N, r)
         facet_ms = kern["facet"][0] / max(1, kern["facet"][1])
         gather_ms = kern["gather"][0] / max(1, kern["gather"][1])
         achieved = fb / (facet_ms * 1e-3) / 1e9

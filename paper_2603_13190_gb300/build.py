@@ -41,7 +41,11 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
-        cmd = [nvcc()] + common + ["-c", os.path.join(CSRC, src), "-o", obj]
+        extra = []
+        if src == "ldpm_kernels.cu":
+            # approximate FP32 division and square root: only the mixed-mode arithmetic is FP32
+            extra = ["-prec-div=false", "-prec-sqrt=false"]
+        cmd = [nvcc()] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, r.stdout, r.stderr))

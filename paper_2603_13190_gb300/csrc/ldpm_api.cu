@@ -160,9 +160,10 @@ void free_model(ldpm_ctx *h)
 {
     for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
-    void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.pm32, h->dm.bc_vel, h->dm.f_ext, h->dm.tet,
+    void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.pm32, h->dm.bc_vel, h->dm.bc_vm, h->dm.f_ext,
+                    h->dm.tet,
                     h->dm.geo,
-                    h->dm.hist, h->dm.fout, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
+                    h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
                     h->dm.step, h->dm.flag, h->d_partial, h->d_out16};
     for (void *p : ptrs)
         if (p) cudaFree(p);
@@ -205,12 +206,11 @@ int check_material(const ldpm_material &m)
 // Per-specimen host preprocessing into the internal layout.  Writes this specimen's slices of the
 // host mirrors of every device array.
 struct HostArrays {
-    std::vector<double> pstate, pdyn, pconst, bc_vel, f_ext;
+    std::vector<double> pstate, pdyn, pconst, bc_vel, bc_vm, f_ext;
     std::vector<int4> tet;
     std::vector<double> geo64;  // [Fint][4] before rounding to R
     std::vector<int32_t> row;
-    std::vector<double> ent64;  // [2 Fint][3] arms
-    std::vector<int64_t> ent_id;
+    std::vector<int64_t> ent_id;  // CSR payload: tetrahedron vertex slot 4 * tet + vertex
     std::vector<int32_t> tile_spec;
     bool any_fext = false;
 };
@@ -309,6 +309,7 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
             pconst_h[8 * P + k] = 1.0 / md[k];
             const double vb = o.bc_vel ? o.bc_vel[6 * (size_t)i + k] : 0.0;
             H.bc_vel[6 * P + k] = vb;
+            H.bc_vm[6 * P + k] = vb * md[k];
             if (o.f_ext) {
                 H.f_ext[6 * P + k] = o.f_ext[6 * (size_t)i + k];
                 H.any_fext = true;
@@ -383,8 +384,6 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
         const double A = 0.5 * std::fabs((dd[0] * nc[0] + dd[1] * nc[1] + dd[2] * nc[2]) / l);
         for (int a = 0; a < 3; ++a) {
             H.geo64[4 * (size_t)fi + a] = xc[a] - xa[a];
-            H.ent64[6 * (size_t)fi + a] = xc[a] - xa[a];      // arm of side 0 (vertex a)
-            H.ent64[6 * (size_t)fi + 3 + a] = xc[a] - xb[a];  // arm of side 1 (vertex b)
         }
         H.geo64[4 * (size_t)fi + 3] = A;
     }
@@ -399,7 +398,7 @@ template <class R>
 int upload_facets(ldpm_ctx *h, const HostArrays &H, int64_t Fint)
 {
     using T4 = R4<R>;
-    std::vector<T4> geo(Fint), ent(2 * Fint);
+    std::vector<T4> geo(Fint);
     for (int64_t f = 0; f < Fint; ++f) {
         geo[f].x = R(H.geo64[4 * f]);
         geo[f].y = R(H.geo64[4 * f + 1]);
@@ -407,25 +406,17 @@ int upload_facets(ldpm_ctx *h, const HostArrays &H, int64_t Fint)
         geo[f].w = R(H.geo64[4 * f + 3]);
     }
     const int64_t nent = H.ent_id.size();
-    for (int64_t r = 0; r < nent; ++r) {
-        const int64_t id = H.ent_id[r];  // facet << 1 | side
-        const int64_t f = id >> 1, side = id & 1;
-        ent[r].x = R(H.ent64[6 * f + 3 * side]);
-        ent[r].y = R(H.ent64[6 * f + 3 * side + 1]);
-        ent[r].z = R(H.ent64[6 * f + 3 * side + 2]);
-        if (sizeof(R) == 4) {
-            const int32_t b = (int32_t)id;
-            std::memcpy(&ent[r].w, &b, 4);
-        } else {
-            std::memcpy(&ent[r].w, &id, 8);
-        }
-    }
+    std::vector<int32_t> ent(nent);
+    for (int64_t r = 0; r < nent; ++r) ent[r] = (int32_t)H.ent_id[r];
     int rc;
+    const int64_t T = Fint / 12;
     if ((rc = dalloc((T4 **)&h->dm.geo, Fint)) || (rc = dalloc((T4 **)&h->dm.hist, Fint)) ||
-        (rc = dalloc((T4 **)&h->dm.fout, Fint)) || (rc = dalloc((T4 **)&h->dm.ent, std::max<int64_t>(nent, 1))))
+        (rc = dalloc((T4 **)&h->dm.fout, Fint)) || (rc = dalloc((R **)&h->dm.tvc, 24 * T)) ||
+        (rc = dalloc((int32_t **)&h->dm.ent, std::max<int64_t>(nent, 1))))
         return rc;
     CU(cudaMemcpy(h->dm.geo, geo.data(), Fint * sizeof(T4), cudaMemcpyHostToDevice));
-    CU(cudaMemcpy(h->dm.ent, ent.data(), nent * sizeof(T4), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.ent, ent.data(), nent * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CU(cudaMemset(h->dm.tvc, 0, 24 * T * sizeof(R)));
     CU(cudaMemset(h->dm.hist, 0, Fint * sizeof(T4)));
     CU(cudaMemset(h->dm.fout, 0, Fint * sizeof(T4)));
     std::vector<LawConst<R>> law(h->sp.size());
@@ -447,7 +438,10 @@ int update_law(ldpm_ctx *h)
         CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(law[0]), cudaMemcpyHostToDevice));
     }
     std::vector<SpecDyn> sd(h->sp.size());
-    for (size_t s = 0; s < h->sp.size(); ++s) sd[s] = SpecDyn{h->sp[s].dt, h->sp[s].ramp_time};
+    for (size_t s = 0; s < h->sp.size(); ++s) {
+        const double T = h->sp[s].ramp_time, dt = h->sp[s].dt;
+        sd[s] = SpecDyn{dt, T, 1.0 / dt, T > 0 ? 1.0 / T : 0.0, 0.5 * dt};
+    }
     CU(cudaMemcpy(h->dm.spec, sd.data(), sd.size() * sizeof(SpecDyn), cudaMemcpyHostToDevice));
     return LDPM_OK;
 }
@@ -612,18 +606,18 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         Np += S.N;
         Tp += S.T_pad;
     }
-    if (Np > INT32_MAX / 2 || 24 * Tp > (int64_t)1 << 30)
-        return fail(LDPM_E_INVALID_ARG, "specimen too large for 32-bit facet-end ids");
+    if (Np > INT32_MAX / 2 || 24 * Tp > (int64_t)INT32_MAX)
+        return fail(LDPM_E_INVALID_ARG, "specimen too large for 32-bit slot ids");
     const int32_t N = (int32_t)Np, T = (int32_t)Tp;
     const int64_t Fint = 12 * (int64_t)T;
     HostArrays H;
     H.pstate.assign(16 * (size_t)N, 0.0);
     H.pdyn.assign(8 * (size_t)N, 0.0);
     H.bc_vel.assign(6 * (size_t)N, 0.0);
+    H.bc_vm.assign(6 * (size_t)N, 0.0);
     H.f_ext.assign(6 * (size_t)N, 0.0);
     H.tet.assign(T, make_int4(-1, -1, -1, -1));
     H.geo64.assign(4 * (size_t)Fint, 0.0);
-    H.ent64.assign(6 * (size_t)Fint, 0.0);
     H.tile_spec.assign(T / kTile, 0);
     h->x_int.assign(3 * (size_t)N, 0.0);
     h->inv_mass.assign(6 * (size_t)N, 0.0);
@@ -637,27 +631,21 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     for (int64_t t = 0; t < T; ++t) {
         const int4 v = H.tet[t];
         if (v.x < 0) continue;
-        const int vv[4] = {v.x, v.y, v.z, v.w};
-        for (int sl = 0; sl < 12; ++sl) {
-            const int e = sl >> 1;
-            H.row[vv[kEdgeA[e]] + 1]++;
-            H.row[vv[kEdgeB[e]] + 1]++;
-        }
+        H.row[v.x + 1]++;
+        H.row[v.y + 1]++;
+        H.row[v.z + 1]++;
+        H.row[v.w + 1]++;
     }
     for (int32_t p = 0; p < N; ++p) H.row[p + 1] += H.row[p];
     H.ent_id.assign(H.row[N], 0);
     {
+        // ascending tetrahedron within each particle: the fixed summation order
         std::vector<int32_t> pos(H.row.begin(), H.row.end() - 1);
         for (int64_t t = 0; t < T; ++t) {
             const int4 v = H.tet[t];
             if (v.x < 0) continue;
             const int vv[4] = {v.x, v.y, v.z, v.w};
-            for (int sl = 0; sl < 12; ++sl) {
-                const int e = sl >> 1;
-                const int64_t f = 12 * t + sl;
-                H.ent_id[pos[vv[kEdgeA[e]]]++] = (f << 1) | 0;
-                H.ent_id[pos[vv[kEdgeB[e]]]++] = (f << 1) | 1;
-            }
+            for (int k = 0; k < 4; ++k) H.ent_id[pos[vv[k]]++] = 4 * t + k;
         }
     }
     // ---- device
@@ -695,9 +683,11 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         const int v = std::atoi(ev);
         if (v == 8 || v == 16 || v == 32) dm.tets_per_block = v;
     }
+    if (const char *ev = std::getenv("LDPM_BLOCKS_PER_SM")) dm.blocks_per_sm = std::max(0, std::atoi(ev));
     int rc;
     if ((rc = dalloc(&dm.pstate, 16 * (size_t)N)) || (rc = dalloc(&dm.pdyn, 8 * (size_t)N)) ||
         (rc = dalloc(&dm.pconst, 8 * (size_t)N)) || (rc = dalloc(&dm.bc_vel, 6 * (size_t)N)) ||
+        (rc = dalloc(&dm.bc_vm, 6 * (size_t)N)) ||
         (rc = dalloc(&dm.tet, (size_t)T)) || (rc = dalloc(&dm.row, (size_t)N + 1)) ||
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
@@ -713,6 +703,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     CU(cudaMemcpy(dm.pdyn, H.pdyn.data(), H.pdyn.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.pconst, h->pconst_h.data(), h->pconst_h.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.bc_vel, H.bc_vel.data(), H.bc_vel.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(dm.bc_vm, H.bc_vm.data(), H.bc_vm.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.tet, H.tet.data(), H.tet.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.row, H.row.data(), H.row.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.tile_spec, H.tile_spec.data(), H.tile_spec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -1073,6 +1064,10 @@ int ldpm_facet_forces(ldpm_t h, double *F3, double *f6)
     if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
     DevGuard dg(h->device);
     try {
+        // per-facet forces are not kept by the step; rebuild them from the stored tractions (this
+        // rewrites the per-vertex shares with the same values)
+        int rc = launch_facet_any(h, FACET_FROM_HIST, nullptr);
+        if (rc) return rc;
         CU(cudaStreamSynchronize(h->stream));
         const int64_t Fint = 12 * (int64_t)h->dm.T;
         std::vector<double> fo(4 * (size_t)Fint), pd(8 * (size_t)h->dm.N);
@@ -1116,7 +1111,7 @@ int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_ti
     if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "ldpm_set_bc applies to single-specimen handles");
     DevGuard dg(h->device);
     SpecHost &S = h->sp[0];
-    std::vector<double> bv(6 * (size_t)h->dm.N, 0.0);
+    std::vector<double> bv(6 * (size_t)h->dm.N, 0.0), bm(6 * (size_t)h->dm.N, 0.0);
     for (int32_t i = 0; i < S.N; ++i) {
         const size_t P = (size_t)S.p0 + S.inv_p[i];
         uint64_t bits = 0;
@@ -1125,6 +1120,7 @@ int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_ti
             if (mk < 0 || mk > 2) return fail(LDPM_E_INVALID_ARG, "bc mask must be 0, 1 or 2");
             bits |= (uint64_t)mk << (8 * k);
             bv[6 * P + k] = vel ? vel[6 * (size_t)i + k] : 0.0;
+            bm[6 * P + k] = bv[6 * P + k] / h->inv_mass[6 * P + k];
         }
         std::memcpy(&h->pconst_h[8 * P + 6], &bits, 8);
     }
@@ -1132,6 +1128,7 @@ int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_ti
     CU(cudaStreamSynchronize(h->stream));
     CU(cudaMemcpy(h->dm.pconst, h->pconst_h.data(), h->pconst_h.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->dm.bc_vel, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CU(cudaMemcpy(h->dm.bc_vm, bm.data(), bm.size() * sizeof(double), cudaMemcpyHostToDevice));
     return update_law(h);
 }
 

@@ -12,9 +12,12 @@
 //   tet    [T]     int4 particle ids of the 4 vertices (-1: padding tetrahedron)
 //   geo    [12T]   R4   c_a (arm from the edge's first vertex to the facet centroid), projected area A
 //   hist   [12T]   R4   t_N, t_M, t_L, e_max
-//   fout   [12T]   R4   facet force acting on the edge's first vertex, 0
-//   row    [N+1]   i32  CSR of facet ends per particle
-//   ent    [2*12T] R4   arm c_s of that end, (facet << 1 | side) stored bit-wise in .w
+//   fout   [12T]   R4   facet force acting on the edge's first vertex, 0 (written only when forces
+//                       are rebuilt from history, for ldpm_facet_forces)
+//   tvc    [T][4][6] R  per tetrahedron vertex: sum of its 6 facets' force (3) and moment about the
+//                       vertex (3), in a fixed order
+//   row    [N+1]   i32  CSR of (tetrahedron, vertex) slots per particle, ascending tetrahedron
+//   ent    [4T]    i32  slot id 4 * tet + vertex
 // Facet slot s of a tetrahedron belongs to edge e = s / 2 with local vertices
 // (a, b) in ((0,1),(0,2),(0,3),(1,2),(1,3),(2,3)); "I" of the internal facet is vertex a.
 #pragma once
@@ -57,6 +60,8 @@ struct LawConst {
 // Per-specimen time integration constants (FP64).
 struct SpecDyn {
     double dt, ramp_time;
+    double inv_dt, inv_ramp;  // 1/dt; 1/ramp_time (0 when ramp_time <= 0: no ramp)
+    double half_dt;
 };
 
 enum FacetMode : int { FACET_STEP = 0, FACET_FROM_HIST = 1, FACET_ELASTIC = 2 };
@@ -69,9 +74,11 @@ struct DeviceModel {
     double *pstate = nullptr, *pdyn = nullptr, *pconst = nullptr;
     float *pm32 = nullptr;          // FP32 mirror (mixed mode), null in FP64 mode
     int32_t gather_lanes = 8;       // lanes per particle in the particle pass (8, 16 or 32)
+    int32_t blocks_per_sm = 0;      // cap on resident facet-pass blocks per SM (0 = occupancy limit)
     double *bc_vel = nullptr, *f_ext = nullptr;
+    double *bc_vm = nullptr;        // [N][6] prescribed velocity times the DOF's mass
     int4 *tet = nullptr;
-    void *geo = nullptr, *hist = nullptr, *fout = nullptr, *ent = nullptr;
+    void *geo = nullptr, *hist = nullptr, *fout = nullptr, *tvc = nullptr, *ent = nullptr;
     int32_t *row = nullptr;
     int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)
     void *law = nullptr;            // LawConst<R>[n_spec]

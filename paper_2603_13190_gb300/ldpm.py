@@ -62,7 +62,8 @@ def lib():
     """Load libldpm.so (building it first if the sources are newer).  Raises if that fails."""
     global _lib
     if _lib is None:
-        path = _build.build()
+        # LDPM_LIBRARY: load an already-built libldpm.so from another path (no build step)
+        path = os.environ.get("LDPM_LIBRARY") or _build.build()
         if not os.path.exists(path):
             raise ImportError("libldpm.so is missing at %s" % path)
         L = C.CDLL(path)
