@@ -210,17 +210,15 @@ def run_ours(args, rank, world, local):
     peak, peak_src = measured_peaks()
     out = {}
     dt0 = None
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.__enter__()
     for prec, steps in (("mixed", args.steps), ("fp64", max(3, args.steps // 4))):
         model = ldpm.Model(spec, wl.material, precision=prec, dt=dt0 or 0.0, bc=bc, stream=stream, device=local)
         dt0 = dt0 or model.dt
         barrier(world)
         torch.cuda.synchronize()
-        sampler = ClockSampler(local) if (rank == 0 and prec == "mixed") else None
-        if sampler:
-            sampler.__enter__()
         ms, _ = time_steps(model, ldpm, torch, stream, flush, steps, args.warmup, profile=False)
-        if sampler:
-            sampler.__exit__()
         torch.cuda.synchronize()
         barrier(world)
         tot = barrier_max(world, sum(ms))
@@ -253,8 +251,11 @@ def run_ours(args, rank, world, local):
                              "algorithmic_bytes_per_launch": gb},
             steady_state={"facet_updates_per_s": world * F / (ss_ms * 1e-3), "ms_per_step": ss_ms,
                           "l2": "not flushed (graph replay, back-to-back)"},
-            energy_err_pct=float(energy[3]), clocks=sampler.summary() if sampler else None, dt=model.dt)
+            energy_err_pct=float(energy[3]), dt=model.dt)
         model.close()
+    if sampler:
+        sampler.__exit__()
+    clocks = sampler.summary() if sampler else None
     # end to end through the C ABI with host buffers: create (H2D of the geometry), K steps each with an
     # energy/reaction read-back (D2H), final state read-back, destroy.
     barrier(world)
@@ -295,8 +296,8 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": d2h / K, "seconds": e2e_s,
                 "what": "ldpm_create from host arrays, K x (ldpm_step(1) + ldpm_energy read-back), "
                         "ldpm_get_state to host, ldpm_destroy"},
-        "gpu_launches": 3 * args.steps,
-        "clocks": mx["clocks"],
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
     }
     return res, spec, wl, bc, dt0
 

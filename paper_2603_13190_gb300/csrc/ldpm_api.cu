@@ -567,6 +567,8 @@ int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
     return LDPM_OK;
 }
 
+int kick(ldpm_ctx *h);
+
 int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, const ldpm_options *opts,
                  ldpm_t *out)
 {
@@ -733,24 +735,29 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         if ((rc = update_law(raw))) return rc;
         CU(cudaMemset(dm.fout, 0, Fint * h->r4size()));
     }
+    // the library keeps the drifted state between calls: first half kick and drift of step 0
+    if ((rc = kick(raw))) return rc;
     CU(cudaDeviceSynchronize());
     guard.armed = false;
     *out = h.release();
     return LDPM_OK;
 }
 
-int enqueue_direct(ldpm_ctx *h, int64_t nsteps, bool with_kick, bool last)
+// nsteps explicit steps on the drifted state: facet pass, then the fused particle pass.
+int enqueue_direct(ldpm_ctx *h, int64_t nsteps)
 {
     int rc;
-    if (with_kick) {
-        cudaError_t e = launch_kick(h->dm, h->stream);
-        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "kick launch: %s", cudaGetErrorString(e));
-    }
     for (int64_t i = 0; i < nsteps; ++i) {
-        const bool lst = last && i == nsteps - 1;
         if ((rc = launch_facet_any(h, FACET_STEP, nullptr))) return rc;
-        if ((rc = launch_gather_any(h, lst ? GATHER_STEP_LAST : GATHER_STEP_MID, nullptr))) return rc;
+        if ((rc = launch_gather_any(h, GATHER_STEP_MID, nullptr))) return rc;
     }
+    return LDPM_OK;
+}
+
+int kick(ldpm_ctx *h)
+{
+    cudaError_t e = launch_kick(h->dm, h->stream);
+    if (e != cudaSuccess) return fail(LDPM_E_CUDA, "kick launch: %s", cudaGetErrorString(e));
     return LDPM_OK;
 }
 
@@ -763,7 +770,7 @@ int graph_for(ldpm_ctx *h, int64_t len, cudaGraphExec_t *exec)
     }
     cudaGraph_t g = nullptr;
     CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
-    int rc = enqueue_direct(h, len, false, false);
+    int rc = enqueue_direct(h, len);
     cudaError_t e = cudaStreamEndCapture(h->stream, &g);
     if (rc) {
         if (g) cudaGraphDestroy(g);
@@ -794,16 +801,10 @@ int enqueue_profiled(ldpm_ctx *h, int64_t nsteps)
         CU(cudaEventRecord(b, h->stream));
         return LDPM_OK;
     };
-    int rc = rec(0, [&]() -> int {
-        cudaError_t e = launch_kick(h->dm, h->stream);
-        return e == cudaSuccess ? LDPM_OK : fail(LDPM_E_CUDA, "kick: %s", cudaGetErrorString(e));
-    });
-    if (rc) return rc;
+    int rc;
     for (int64_t i = 0; i < nsteps; ++i) {
-        const bool lst = i == nsteps - 1;
         if ((rc = rec(1, [&]() { return launch_facet_any(h, FACET_STEP, nullptr); }))) return rc;
-        if ((rc = rec(2, [&]() { return launch_gather_any(h, lst ? GATHER_STEP_LAST : GATHER_STEP_MID, nullptr); })))
-            return rc;
+        if ((rc = rec(2, [&]() { return launch_gather_any(h, GATHER_STEP_MID, nullptr); }))) return rc;
     }
     return LDPM_OK;
 }
@@ -900,20 +901,18 @@ int ldpm_step(ldpm_t h, int64_t nsteps)
     DevGuard dg(h->device);
     try {
         if (h->prof) return enqueue_profiled(h, nsteps);
-        if (h->graph_chunk < 0) return enqueue_direct(h, nsteps, true, true);
+        if (h->graph_chunk < 0) return enqueue_direct(h, nsteps);
         int rc;
-        cudaError_t e = launch_kick(h->dm, h->stream);
-        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "kick launch: %s", cudaGetErrorString(e));
-        int64_t mid = nsteps - 1;
+        int64_t left = nsteps;
         const int64_t chunk = std::max(1, h->graph_chunk);
-        while (mid > 0) {
-            const int64_t len = std::min(mid, chunk);
+        while (left > 0) {
+            const int64_t len = std::min(left, chunk);
             cudaGraphExec_t ex;
             if ((rc = graph_for(h, len, &ex))) return rc;
             CU(cudaGraphLaunch(ex, h->stream));
-            mid -= len;
+            left -= len;
         }
-        return enqueue_direct(h, 1, false, true);
+        return LDPM_OK;
     } catch (...) {
         return fail(LDPM_E_CUDA, "unexpected exception in ldpm_step");
     }
@@ -937,6 +936,17 @@ int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
         std::vector<double> ps, h5;
         int rc = download_state(h, ps, hist5 ? &h5 : nullptr);
         if (rc) return rc;
+        // whole-step q_n, v_n from the drifted state
+        std::vector<double> qv(12 * (size_t)h->dm.N);
+        double *d12 = nullptr;
+        if ((rc = dalloc(&d12, qv.size()))) return rc;
+        cudaError_t e = launch_unkick(h->dm, d12, h->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(qv.data(), d12, qv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+        cudaError_t e2 = cudaStreamSynchronize(h->stream);
+        cudaFree(d12);
+        if (e != cudaSuccess || e2 != cudaSuccess)
+            return fail(LDPM_E_CUDA, "state read-back: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
         int64_t st = 0;
         CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
         size_t base_p = 0, base_f = 0;
@@ -944,8 +954,8 @@ int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
             for (int32_t i = 0; i < S.N; ++i) {
                 const size_t P = (size_t)S.p0 + S.inv_p[i];
                 for (int k = 0; k < 6; ++k) {
-                    if (q) q[6 * (base_p + i) + k] = ps[16 * P + 3 + k];
-                    if (v) v[6 * (base_p + i) + k] = ps[16 * P + 9 + k];
+                    if (q) q[6 * (base_p + i) + k] = qv[12 * P + k];
+                    if (v) v[6 * (base_p + i) + k] = qv[12 * P + 6 + k];
                 }
             }
             if (hist5)
@@ -1021,7 +1031,10 @@ int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *his
             return fail(LDPM_E_CUDA, "history upload: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
         CU(cudaMemcpy(h->dm.step, &step, sizeof(step), cudaMemcpyHostToDevice));
         CU(cudaMemset(h->dm.flag, 0, sizeof(int32_t)));
-        return forces_from_history(h);
+        if ((rc = forces_from_history(h))) return rc;
+        if ((rc = kick(h))) return rc;
+        CU(cudaStreamSynchronize(h->stream));
+        return LDPM_OK;
     } catch (const std::bad_alloc &) {
         return fail(LDPM_E_OOM, "host allocation failed");
     }
@@ -1125,11 +1138,17 @@ int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_ti
         std::memcpy(&h->pconst_h[8 * P + 6], &bits, 8);
     }
     S.ramp_time = ramp_time;
+    // back to the whole-step state under the old conditions, then forward under the new ones
+    CU(launch_unkick(h->dm, nullptr, h->stream));
     CU(cudaStreamSynchronize(h->stream));
     CU(cudaMemcpy(h->dm.pconst, h->pconst_h.data(), h->pconst_h.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->dm.bc_vel, bv.data(), bv.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(h->dm.bc_vm, bm.data(), bm.size() * sizeof(double), cudaMemcpyHostToDevice));
-    return update_law(h);
+    int rc = update_law(h);
+    if (rc) return rc;
+    if ((rc = kick(h))) return rc;
+    CU(cudaStreamSynchronize(h->stream));
+    return LDPM_OK;
 }
 
 int ldpm_info(ldpm_t h, int64_t info[5], double *dt)

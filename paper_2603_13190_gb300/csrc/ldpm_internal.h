@@ -3,7 +3,8 @@
 //
 // Device layout (all arrays in the library's internal order: particles and tetrahedra sorted along a
 // Morton curve, facets tetrahedron-major with 12 consecutive slots per tetrahedron):
-//   pstate [N][16] f64  x(3) q(6) v(6) pad      gathered by the facet pass (one 128-byte line)
+//   pstate [N][16] f64  x(3) q(6) v(6) pad      gathered by the facet pass (one 128-byte line);
+//                       between calls q = q_{n+1} and v = v_{n+1/2} (drifted state of step n)
 //   pdyn   [N][8]  f64  f_asm(6) W_int W_ext     node force sums of the current step, energy sums
 //   pconst [N][8]  f64  1/mass(6) bc-bits spec   per-DOF inverse mass, 8-bit BC code per DOF, specimen
 //   pm32   [N][24] f32  mixed mode only: FP32 mirror read by the facet pass, written by the particle
@@ -65,7 +66,7 @@ struct SpecDyn {
 };
 
 enum FacetMode : int { FACET_STEP = 0, FACET_FROM_HIST = 1, FACET_ELASTIC = 2 };
-enum GatherMode : int { GATHER_ASSEMBLE = 0, GATHER_STEP_MID = 1, GATHER_STEP_LAST = 2 };
+enum GatherMode : int { GATHER_ASSEMBLE = 0, GATHER_STEP_MID = 1 };
 
 struct DeviceModel {
     int32_t N = 0, T = 0;     // T includes padding tetrahedra
@@ -91,7 +92,10 @@ struct DeviceModel {
 void set_last_error(const char *msg);
 
 // Launchers (ldpm_kernels.cu).  All enqueue on `s` and return the launch error.
+// kick: whole-step state (q_n, v_n, f_n) -> drifted state (q_{n+1}, v_{n+1/2}) kept between calls.
 cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s);
+// unkick: the inverse; into out12 [N][12] (q_n then v_n) or, with out12 null, in place.
+cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s);
 // `src_override` replaces the particle records the facet pass reads (FP64 mode: pstate layout;
 // mixed mode: pm32 layout); null = the model's own.
 template <class R>

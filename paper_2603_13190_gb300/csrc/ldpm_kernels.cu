@@ -1,6 +1,8 @@
 // ldpm_kernels.cu -- sm_103a kernels of the LDPM explicit central-difference step.
 //
-// One step (paper Sec. 3, central difference with lumped mass) is two launches in steady state:
+// One step (paper Sec. 3, central difference with lumped mass) is two launches.  Between steps the
+// state is kept drifted: q_{n+1} and v_{n+1/2} (and f_n); kick_kernel / unkick_kernel convert from /
+// to the whole-step state q_n, v_n at the API boundary.
 //   facet_kernel   per facet: rigid-body jump and strain (Sec. 2, Eq. (1)), per-tetrahedron
 //                  volumetric strain (App. A.2 e_V), the Appendix A law, force A P t; then per
 //                  tetrahedron vertex the fixed-order sum of its 6 facets' forces and moments
@@ -667,12 +669,10 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
     const double hdq = hdt * vh;
     double dWi = act ? -(fa_old + fa_new) * hdq : 0.0;
     double dWe = (need_we && act) ? g_sum * hdq : 0.0;
-    double q = ps[3 + d];
-    double v_store = v_new;
-    if (MODE != GATHER_STEP_LAST) {
-        v_store = v_next;
-        q += dt * v_next;
-    }
+    // store the drifted state of the next step: v_{n+3/2} and q_{n+2} = q_{n+1} + dt v_{n+3/2}
+    (void)v_new;
+    const double v_store = v_next;
+    const double q = ps[3 + d] + dt * v_next;
     // sum the six DOF contributions into lane 0 of the group (lanes 6, 7 hold zeros)
 #pragma unroll
     for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
@@ -682,7 +682,7 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
     }
     if (act) {
         pd[d] = fa_new;
-        if (MODE != GATHER_STEP_LAST) ps[3 + d] = q;
+        ps[3 + d] = q;
         ps[9 + d] = v_store;
         if (m.pm32) write_mirror(m.pm32 + kMirror * pc_, d, q, v_store);
         if (!finite_bits(v_store) || !finite_bits(q)) *(volatile int32_t *)m.flag = 1;
@@ -721,6 +721,40 @@ __global__ void __launch_bounds__(256) kick_kernel(DeviceModel m)
     if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, q, vh);
 }
 
+// Whole-step state (q_n, v_n) from the drifted state (q_{n+1}, v_{n+1/2}) the library keeps between
+// calls: the inverse of kick_kernel under the same boundary conditions.  out12 [N][12] (q then v),
+// or null to rewrite pstate (and the mirror) in place.
+__global__ void __launch_bounds__(256) unkick_kernel(DeviceModel m, double *__restrict__ out12)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * (int64_t)m.N) return;
+    const int64_t p = i / 6;
+    const int d = (int)(i - 6 * p);
+    double *ps = m.pstate + 16 * p;
+    const double *pc = m.pconst + 8 * p;
+    const int mask = (int)(((uint64_t)__double_as_longlong(pc[6]) >> (8 * d)) & 0xffu);
+    const SpecDyn &S = m.spec[(int)__double_as_longlong(pc[7])];
+    const double vh = ps[9 + d];
+    double vn;
+    if (mask == 0) {
+        const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
+        vn = vh - S.half_dt * (fe + m.pdyn[8 * p + d]) * pc[d];
+    } else if (mask == 1) {
+        vn = 0.0;
+    } else {
+        vn = m.bc_vel[6 * p + d] * ramp((double)(*m.step) * S.dt, S.inv_ramp);
+    }
+    const double qn = ps[3 + d] - S.dt * vh;
+    if (out12) {
+        out12[12 * p + d] = qn;
+        out12[12 * p + 6 + d] = vn;
+    } else {
+        ps[3 + d] = qn;
+        ps[9 + d] = vn;
+        if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, qn, vn);
+    }
+}
+
 // FP32 mirror of every particle from the FP64 records.
 __global__ void __launch_bounds__(256) mirror_kernel(DeviceModel m)
 {
@@ -755,7 +789,15 @@ __global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, 
         acc[1] = pd[7];
         for (int d = 0; d < 6; ++d) {
             const double mass = 1.0 / pc[d];
-            const double v = ps[9 + d];
+            // whole-step velocity v_n from the stored v_{n+1/2} (inverse half kick)
+            const int mk = (int)((bcbits >> (8 * d)) & 0xffu);
+            double v = ps[9 + d];
+            if (mk == 0)
+                v -= S.half_dt * ((m.f_ext ? m.f_ext[6 * p + d] : 0.0) + pd[d]) * pc[d];
+            else if (mk == 1)
+                v = 0.0;
+            else
+                v = m.bc_vel[6 * p + d] * ramp(t, S.inv_ramp);
             acc[2] += 0.5 * mass * v * v;
             const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
             if (mask == 1) {
@@ -892,6 +934,14 @@ cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t
 
 }  // namespace
 
+cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s)
+{
+    const int64_t n = 6 * (int64_t)m.N;
+    if (n == 0) return cudaSuccess;
+    unkick_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, out12);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s)
 {
     const int64_t n = 6 * (int64_t)m.N;
@@ -924,9 +974,6 @@ cudaError_t launch_gather_lpp(const DeviceModel &m, int mode, double *out6, cuda
     switch (mode) {
     case GATHER_ASSEMBLE:
         gather_kernel<R, GATHER_ASSEMBLE, LPP><<<blocks, 256, 0, s>>>(m, out6);
-        break;
-    case GATHER_STEP_LAST:
-        gather_kernel<R, GATHER_STEP_LAST, LPP><<<blocks, 256, 0, s>>>(m, out6);
         break;
     default:
         gather_kernel<R, GATHER_STEP_MID, LPP><<<blocks, 256, 0, s>>>(m, out6);
