@@ -160,6 +160,14 @@ int ldpm_energy(ldpm_t h, double out[4], double reaction[12]);
  * f6 [N][6] per-particle sums of facet forces and moments.  Either pointer may be NULL. */
 int ldpm_facet_forces(ldpm_t h, double *F3, double *f6);
 
+/* Post-processing fields of the current state (synchronises).  crack_opening [F] (caller facet
+ * order): w = sqrt(w_N^2 + w_M^2 + w_L^2) per facet, the comparison field of Sec. 4, with only
+ * positive inelastic normal strain opening the crack; the paper gives no formula for w_alpha, the
+ * library takes the inelastic part of the jump, w_N = l <e_N - t_N/E0>, w_M,L = l (e_M,L - t_M,L /
+ * (alpha E0)).  tet_volumetric_strain [T] (caller tetrahedron order): e_V of App. A.2, the field
+ * compared for the uniaxial-strain test (Sec. 4.2).  Either pointer may be NULL. */
+int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain);
+
 /* Replace the boundary conditions (takes effect for steps enqueued afterwards).  mask [N][6],
  * vel [N][6] (NULL = zeros), ramp measured from t = 0. */
 int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_time);

@@ -58,6 +58,8 @@ def lib():
         L.orc_geometry.argtypes = [P, P, P, P, P, P, P]
         L.orc_facet_law.argtypes = [C.POINTER(OrcMaterial), D, P, P, D, P, D, P, P]
         L.orc_facet_march.argtypes = [C.POINTER(OrcMaterial), D, I64, P, P, P, P]
+        L.orc_metrics.argtypes = [P, P, P]
+        L.orc_set_bc.argtypes = [P, P, P, D]
         _lib = L
     return _lib
 
@@ -188,6 +190,19 @@ class Oracle:
     def critical_dt(self, seed: int = 0, iters: int = 300) -> float:
         x0 = np.random.default_rng(seed).standard_normal(6 * self.N)
         return 2.0 / np.sqrt(self.lambda_max(x0, iters))
+
+    def metrics(self):
+        """Crack opening per facet and volumetric strain per tetrahedron of the current state."""
+        w = np.zeros(self.F)
+        eV = np.zeros(max(self.T, 1))
+        lib().orc_metrics(self.h, _p(w), _p(eV))
+        return w, eV[: self.T]
+
+    def set_bc(self, bc) -> None:
+        mask = np.ascontiguousarray(bc.mask, np.int32)
+        vel = np.ascontiguousarray(bc.vel, np.float64)
+        self._keep += [mask, vel]
+        lib().orc_set_bc(self.h, _p(mask), _p(vel), float(bc.ramp_time))
 
     def geometry(self):
         n = np.zeros((self.F, 3))

@@ -666,3 +666,41 @@ void orc_facet_march(const orc_material *p, double l, int64_t n, const double *p
         emax_out[i] = em;
     }
 }
+
+/* Crack opening per facet (Sec. 4: w = sqrt(w_N^2 + w_M^2 + w_L^2), only positive inelastic normal
+ * strain opening the crack).  The paper gives no formula for w_alpha; the reading used is the
+ * inelastic part of the facet displacement jump: w_N = l <e_N - t_N / E0>, w_M = l (e_M - t_M / (alpha
+ * E0)), w_L = l (e_L - t_L / (alpha E0)).  Also the volumetric strain of every tetrahedron (the field
+ * the paper compares for the uniaxial-strain test).  Both at the current state. */
+void orc_metrics(const orc_model *M, double *w, double *eV)
+{
+    const double E0 = M->mat.E0, aE = M->mat.alpha * M->mat.E0;
+    if (w)
+        for (int32_t k = 0; k < M->F; ++k) {
+            const double *e = M->e_prev + 3 * (size_t)k, *t = M->t_loc + 3 * (size_t)k;
+            double wn = e[0] - t[0] / E0;
+            if (wn < 0.0) wn = 0.0;
+            double wm = e[1] - t[1] / aE, wl = e[2] - t[2] / aE;
+            w[k] = M->len[k] * sqrt(wn * wn + wm * wm + wl * wl);
+        }
+    if (eV)
+        for (int32_t t = 0; t < M->T; ++t) eV[t] = tet_volumetric_strain(M, M->q, t);
+}
+
+/* Replace the boundary conditions (mask, velocities, ramp) for the following steps.  Velocities of
+ * newly fixed or prescribed DOFs take their constrained values at the current time. */
+void orc_set_bc(orc_model *M, const int32_t *mask, const double *vel, double ramp_time)
+{
+    size_t n6 = 6 * (size_t)M->N;
+    memcpy(M->bc_mask, mask, sizeof(int32_t) * n6);
+    if (vel)
+        memcpy(M->bc_vel, vel, sizeof(double) * n6);
+    else
+        memset(M->bc_vel, 0, sizeof(double) * n6);
+    M->ramp_time = ramp_time;
+    double t = (double)M->step * M->dt;
+    for (size_t i = 0; i < n6; ++i) {
+        if (M->bc_mask[i] == 1) M->v[i] = 0.0;
+        if (M->bc_mask[i] == 2) M->v[i] = M->bc_vel[i] * ramp(M, t);
+    }
+}

@@ -127,6 +127,7 @@ struct SpecHost {
     std::vector<int32_t> perm_p;  // internal rank -> caller particle
     std::vector<int32_t> inv_p;   // caller particle -> internal rank
     std::vector<int64_t> fmap;    // caller facet -> internal facet (global index)
+    std::vector<int32_t> tmap;    // caller tetrahedron -> internal tetrahedron (global index)
     std::vector<uint8_t> fswap;   // caller facet I is the internal b vertex
 };
 
@@ -274,6 +275,8 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     std::iota(perm_t.begin(), perm_t.end(), 0);
     std::stable_sort(perm_t.begin(), perm_t.end(), [&](int32_t a, int32_t b) { return tkey[a] < tkey[b]; });
     for (int32_t r = 0; r < T; ++r) inv_t[perm_t[r]] = r;
+    S.tmap.resize(T);
+    for (int32_t t = 0; t < T; ++t) S.tmap[t] = S.t0 + inv_t[t];
 
     // ---- particles: positions, lumped mass (Sec. 3.2.5), BCs, initial velocity
     std::vector<double> mass(N, 0.0);
@@ -1110,6 +1113,42 @@ int ldpm_facet_forces(ldpm_t h, double *F3, double *f6)
                 }
             base_p += S.N;
             base_f += S.F;
+        }
+        return LDPM_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
+int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    try {
+        int rc = launch_facet_any(h, FACET_METRIC, nullptr);
+        if (rc) return rc;
+        CU(cudaStreamSynchronize(h->stream));
+        const int64_t Fint = 12 * (int64_t)h->dm.T;
+        std::vector<double> fo(4 * (size_t)Fint);
+        if (h->prec == LDPM_MIXED) {
+            std::vector<float4> t(Fint);
+            CU(cudaMemcpy(t.data(), h->dm.fout, Fint * sizeof(float4), cudaMemcpyDeviceToHost));
+            for (int64_t f = 0; f < Fint; ++f) {
+                fo[4 * f] = t[f].x;
+                fo[4 * f + 1] = t[f].y;
+            }
+        } else {
+            CU(cudaMemcpy(fo.data(), h->dm.fout, Fint * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+        }
+        size_t base_f = 0, base_t = 0;
+        for (auto &S : h->sp) {
+            if (crack_opening)
+                for (int32_t k = 0; k < S.F; ++k) crack_opening[base_f + k] = fo[4 * (size_t)S.fmap[k]];
+            if (tet_volumetric_strain)
+                for (int32_t t = 0; t < S.T; ++t) tet_volumetric_strain[base_t + t] = fo[4 * (12 * (size_t)S.tmap[t]) + 1];
+            base_f += S.F;
+            base_t += S.T;
         }
         return LDPM_OK;
     } catch (const std::bad_alloc &) {

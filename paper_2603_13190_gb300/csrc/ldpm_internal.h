@@ -65,7 +65,9 @@ struct SpecDyn {
     double half_dt;
 };
 
-enum FacetMode : int { FACET_STEP = 0, FACET_FROM_HIST = 1, FACET_ELASTIC = 2 };
+// FACET_METRIC: crack opening and tetrahedron volumetric strain of the whole-step state, written to
+// fout (.x = w per facet, .y = e_V of the facet's tetrahedron); history unchanged.
+enum FacetMode : int { FACET_STEP = 0, FACET_FROM_HIST = 1, FACET_ELASTIC = 2, FACET_METRIC = 3 };
 enum GatherMode : int { GATHER_ASSEMBLE = 0, GATHER_STEP_MID = 1 };
 
 struct DeviceModel {

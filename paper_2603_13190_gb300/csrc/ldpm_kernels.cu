@@ -323,6 +323,14 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
                 o[12 + k] = rec[12 + k];
             }
         }
+        if (MODE == FACET_METRIC) {  // whole-step state: u_n = u_{n+1} - dt v_{n+1/2}, same for theta
+            const R dtm = lawc[m.tile_spec ? m.tile_spec[tet0 / 32] : 0].dt;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                o[3 + k] -= dtm * o[6 + k];
+                o[9 + k] -= dtm * o[12 + k];
+            }
+        }
         o[15] = R(0);
 #pragma unroll
         for (int k = 0; k < kRow; k += E) VecT<R>::put(&sv[tid][k], &o[k]);
@@ -393,6 +401,20 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
                 tN = c.E0 * e3.x;
                 tM = c.alpha * c.E0 * e3.y;
                 tL = c.alpha * c.E0 * e3.z;
+            } else if (MODE == FACET_METRIC) {
+                // crack opening from the inelastic part of the jump: w_N = l <e_N - t_N / E0>,
+                // w_T = l (e_T - t_T / (alpha E0)) (u here is already u_n)
+                R wn = e3.x - h.x / c.E0;
+                wn = wn > R(0) ? wn : R(0);
+                const R aE = c.alpha * c.E0;
+                const R wm = e3.y - h.y / aE, wl = e3.z - h.z / aE;
+                T4 o4;
+                o4.x = l * sqrt(wn * wn + wm * wm + wl * wl);
+                o4.y = seV[j];
+                o4.z = R(0);
+                o4.w = R(0);
+                fout[f] = o4;
+                tN = tM = tL = R(0);
             } else {
                 const V3<R> omA = {A[12], A[13], A[14]}, omB = {B[12], B[13], B[14]};
                 const V3<R> dv = {B[6] - A[6], B[7] - A[7], B[8] - A[8]};
@@ -445,7 +467,7 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 
     // ---- phase C: thread `slot` of tetrahedron j sums components 2 q, 2 q + 1 (q = slot % 3) of
     // vertex v = slot / 3 over its 3 edges (ascending), each edge's two facets in slot order.
-    if (live) {
+    if (live && MODE != FACET_METRIC) {
         const int v = slot / 3;
         const int q = slot - 3 * v;
         const int edges = (int)((0x542531430210ull >> (12 * v)) & 0xFFF);
@@ -961,6 +983,8 @@ cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_overrid
         return launch_facet_tpb<R, FACET_FROM_HIST>(m, pst, s);
     case FACET_ELASTIC:
         return launch_facet_tpb<R, FACET_ELASTIC>(m, pst, s);
+    case FACET_METRIC:
+        return launch_facet_tpb<R, FACET_METRIC>(m, pst, s);
     default:
         return launch_facet_tpb<R, FACET_STEP>(m, pst, s);
     }

@@ -77,6 +77,7 @@ def lib():
             "ldpm_energy": ([P, P, P], C.c_int),
             "ldpm_facet_forces": ([P, P, P], C.c_int),
             "ldpm_set_bc": ([P, P, P, D], C.c_int),
+            "ldpm_metrics": ([P, P, P], C.c_int),
             "ldpm_info": ([P, P, P], C.c_int),
             "ldpm_profile": ([P, I32], C.c_int),
             "ldpm_profile_read": ([P, P, P, I32], C.c_int),
@@ -191,6 +192,13 @@ def ldpm_facet_forces(h, N: int, F: int):
     return F3, f6
 
 
+def ldpm_metrics(h, F: int, T: int):
+    w = np.zeros(F)
+    eV = np.zeros(T)
+    _check(lib().ldpm_metrics(h, _ptr(w), _ptr(eV)), "ldpm_metrics")
+    return w, eV
+
+
 def ldpm_set_bc(h, mask, vel, ramp_time: float) -> None:
     mask = np.ascontiguousarray(mask, np.int32)
     vel = None if vel is None else np.ascontiguousarray(vel, np.float64)
@@ -289,6 +297,9 @@ class Model:
 
     def set_bc(self, mask, vel, ramp_time):
         ldpm_set_bc(self.h, mask, vel, ramp_time)
+
+    def metrics(self):
+        return ldpm_metrics(self.h, self.F, self.T)
 
     def info(self):
         return ldpm_info(self.h)

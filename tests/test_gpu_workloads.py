@@ -1,0 +1,145 @@
+"""GPU against the FP64 oracle on workload-scale cases: metrics, boundary-condition switches, the
+mixed-mode trajectory tolerances, and one-step parity at the full and maximum specimen sizes.
+
+Mixed-mode trajectory tolerances (the precision contract of the mixed mode):
+  pre-peak macroscopic stress within 1e-3 (relative to the oracle's, where above 10 % of the peak),
+  energy-balance error (Sec. 4) within 1 %,
+  post-peak crack openings (Sec. 4): Pearson correlation >= 0.99 and NRMSE <= 5 % (normalised by the
+  oracle's largest opening).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_13190_gb300 import ldpm, specimen, workloads
+from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
+
+pytestmark = pytest.mark.gpu
+MAT = dict(WORKLOAD_MATERIAL)
+
+
+def nrel(a, b):
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
+
+
+def oracle_dt(spec, mat, bc, factor=0.9):
+    return factor * oracle.Oracle(spec, mat, 1e-7, bc).critical_dt()
+
+
+@pytest.fixture(scope="module")
+def cracked():
+    """12 mm cube pulled and sheared past its peak by the oracle."""
+    spec = specimen.shuffled(specimen.make_cube_specimen(12.0, 2.0, 4.0, 300, seed=21), seed=5)
+    bc = workloads.uniaxial_tension_bc(spec, velocity=200.0, ramp_time=1e-5)
+    top = spec.face_nodes(2, 1)
+    bc.mask[top, 1] = workloads.PRESCRIBED
+    bc.vel[top, 1] = 60.0
+    dt = oracle_dt(spec, MAT, bc)
+    o = oracle.Oracle(spec, MAT, dt, bc)
+    o.step(900)
+    return spec, bc, dt, o
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-4)])
+def test_metrics_parity(cracked, prec, tol):
+    spec, bc, dt, o = cracked
+    q, v, h5, st = o.get_state()
+    m = ldpm.Model(spec, MAT, precision=prec, dt=dt, bc=bc)
+    m.set_state(q, v, h5, st)
+    wg, eVg = m.metrics()
+    wo, eVo = o.metrics()
+    assert wo.max() > 0, "the fixture must contain cracked facets"
+    assert nrel(wg, wo) <= tol and nrel(eVg, eVo) <= tol, (nrel(wg, wo), nrel(eVg, eVo))
+
+
+def test_boundary_condition_switch_parity_fp64():
+    """Confined compression: hydrostatic phase, then lateral faces held (ldpm_set_bc), both sides."""
+    spec = specimen.make_cube_specimen(12.0, 2.0, 4.0, 300, seed=22)
+    bc1 = workloads.confined_compression_bc(spec, velocity=400.0, phase=1, ramp_time=1e-5)
+    bc2 = workloads.confined_compression_bc(spec, velocity=400.0, phase=2, ramp_time=1e-5)
+    dt = oracle_dt(spec, MAT, bc1)
+    o = oracle.Oracle(spec, MAT, dt, bc1)
+    m = ldpm.Model(spec, MAT, precision="fp64", dt=dt, bc=bc1)
+    o.step(150)
+    m.step(150)
+    o.set_bc(bc2)
+    m.set_bc(bc2.mask, bc2.vel, bc2.ramp_time)
+    o.step(150)
+    m.step(150)
+    qg, vg, hg, _ = m.get_state()
+    qo, vo, ho, _ = o.get_state()
+    assert nrel(qg, qo) <= 1e-9 and nrel(vg, vo) <= 1e-9 and nrel(hg, ho) <= 1e-9
+    eg, rg = m.energy()
+    eo, ro = o.energy()
+    assert nrel(eg[:3], eo[:3]) <= 1e-9 and nrel(rg, ro) <= 1e-9
+    assert ho[:, 0].min() < -0.5 * MAT["sigma_c0"], "compression must reach the compressive boundary"
+
+
+def test_mixed_tension_trajectory_meets_tolerances():
+    spec = specimen.make_cube_specimen(12.0, 2.0, 4.0, 320, seed=23)
+    bc = workloads.uniaxial_tension_bc(spec, velocity=50.0, ramp_time=1e-5)
+    dt = oracle_dt(spec, MAT, bc)
+    o = oracle.Oracle(spec, MAT, dt, bc)
+    m = ldpm.Model(spec, MAT, precision="mixed", dt=dt, bc=bc)
+    so, sg, eo_err, eg_err = [], [], [], []
+    for _ in range(160):
+        o.step(10)
+        m.step(10)
+        eo, ro = o.energy()
+        eg, rg = m.energy()
+        so.append(ro[8] / spec.edge ** 2)
+        sg.append(rg[8] / spec.edge ** 2)
+        eo_err.append(eo[3])
+        eg_err.append(eg[3])
+    so, sg = np.array(so), np.array(sg)
+    k = int(np.argmax(so))
+    assert 0 < k < len(so) - 20 and so[-1] < 0.6 * so[k], "run must pass the peak and soften"
+    pre = slice(0, k + 1)
+    big = so[pre] > 0.1 * so[k]
+    assert np.max(np.abs(sg[pre][big] - so[pre][big]) / so[pre][big]) <= 1e-3
+    assert max(eg_err[5:]) <= 1.0 and max(eo_err[5:]) <= 1.0
+    wo, _ = o.metrics()
+    wg, _ = m.metrics()
+    corr = np.corrcoef(wo, wg)[0, 1]
+    nrmse = 100.0 / wo.max() * np.sqrt(np.mean((wo - wg) ** 2))
+    assert corr >= 0.99 and nrmse <= 5.0, (corr, nrmse)
+
+
+def _full_size_one_step(name, steps_before, velocity, prec_tols):
+    wl = workloads.WORKLOADS[name]
+    spec = wl.specimen()
+    if name == "uniaxial_tension":
+        bc = workloads.uniaxial_tension_bc(spec, velocity=velocity, ramp_time=2e-6)
+    else:
+        bc = workloads.confined_compression_bc(spec, velocity=velocity, phase=1, ramp_time=2e-6)
+    dt = 1.8e-7 if name == "uniaxial_tension" else 2.5e-7  # below the critical step of either cube
+    o = oracle.Oracle(spec, wl.material, dt, bc)
+    o.step(steps_before)
+    q, v, h5, st = o.get_state()
+    o.step(1)
+    qo, vo, ho, _ = o.get_state()
+    Fo, fo = o.facet_forces()
+    for prec, tol in prec_tols:
+        m = ldpm.Model(spec, wl.material, precision=prec, dt=dt, bc=bc)
+        m.set_state(q, v, h5, st)
+        m.step(1)
+        qg, vg, hg, _ = m.get_state()
+        Fg, fg = m.facet_forces()
+        assert nrel(fg, fo) <= tol and nrel(vg, vo) <= tol and nrel(qg, qo) <= tol, (prec, nrel(fg, fo))
+        if prec == "fp64":
+            assert nrel(hg, ho) <= tol and nrel(Fg, Fo) <= tol
+        else:
+            err = np.abs(Fg - Fo).max(axis=1) / np.abs(Fo).max()
+            assert np.mean(err > 1e-4) < 5e-3
+        m.close()
+
+
+def test_full_size_uniaxial_tension_one_step():
+    """The benchmark specimen (1.82M facets) in both precisions, one step from an oracle state."""
+    _full_size_one_step("uniaxial_tension", 12, 2000.0, [("fp64", 1e-10), ("mixed", 2e-5)])
+
+
+def test_max_size_confined_compression_one_step():
+    """The largest workload (12.5M facets), one step from an oracle state, both precisions."""
+    _full_size_one_step("confined_compression", 4, 2000.0, [("fp64", 1e-10), ("mixed", 2e-5)])

@@ -147,3 +147,38 @@ def test_frame_rotation_invariance_of_forces():
             o.step(1)
         outs.append(o.facet_forces()[1])
     np.testing.assert_allclose(outs[0], outs[1], rtol=0, atol=1e-9 * np.abs(outs[0]).max())
+
+
+def test_crack_opening_zero_while_elastic_and_equal_to_jump_when_separated():
+    """w (Sec. 4) vanishes on an elastic state and equals the opening |[[u]]| of a fully separated
+    facet (traction decayed to zero, App. A.1)."""
+    import math
+    from paper_2603_13190_gb300.specimen import Specimen
+    l, h = 3.0, 2.0
+    x = np.array([[0.0, 0.0, 0.0], [l, 0.0, 0.0]])
+    vtx = np.array([[l / 2, -h / 3, -h / 3, l / 2, 2 * h / 3, -h / 3, l / 2, -h / 3, 2 * h / 3]])
+    spec = Specimen(x=x, diameter=np.ones(2), tets=np.zeros((0, 4), np.int32), facet_pi=np.array([0], np.int32),
+                    facet_pj=np.array([1], np.int32), facet_tet=np.array([-1], np.int32), facet_vtx=vtx, edge=l,
+                    d_min=1.0, d_max=1.0)
+    o = oracle.Oracle(spec, MAT, 1e-7, mass=np.full(2, 1e-6), inertia=np.full((2, 3), 1e-7))
+    q = np.zeros((2, 6))
+    q[1, 0] = 0.5 * MAT["sigma_t"] / MAT["E0"] * l  # half the peak strain: elastic
+    o.set_state(q, np.zeros((2, 6)), np.zeros((1, 5)))
+    o.set_state(q, np.zeros((2, 6)), np.array([[MAT["E0"] * q[1, 0] / l, 0, 0, 0, 0]]))
+    w, _ = o.metrics()
+    assert w[0] < 1e-12 * q[1, 0]
+    # fully separated: traction zero, opening (0.02, 0.01, 0) mm
+    q[1, :3] = [0.02, 0.01, 0.0]
+    o.set_state(q, np.zeros((2, 6)), np.array([[0.0, 0, 0, 0, 1.0]]))
+    w, _ = o.metrics()
+    assert abs(w[0] - math.hypot(0.02, 0.01)) < 1e-14
+
+
+def test_volumetric_strain_metric_is_trace_over_three(cube):
+    spec, o = cube
+    rng = np.random.default_rng(6)
+    A = rng.standard_normal((3, 3)) * 1e-4
+    eps = 0.5 * (A + A.T)
+    o.set_state(affine_q(spec, eps), np.zeros((spec.n_particles, 6)), np.zeros((spec.n_facets, 5)))
+    _, eV = o.metrics()
+    np.testing.assert_allclose(eV, np.trace(eps) / 3.0, rtol=1e-10)
