@@ -116,7 +116,10 @@ typedef struct {
     const double *v0;       /* [N][6] initial velocity or NULL */
     const double *f_ext;    /* [N][6] constant external nodal forces or NULL */
     int32_t device;         /* CUDA device ordinal; < 0 = the current device */
-    int32_t reserved;       /* must be 0 */
+    int32_t autotune;       /* 1: at create, time the launch shapes (tetrahedra per facet-pass block,
+                               lanes per particle) on this model and keep the fastest; 0: defaults.
+                               Results are deterministic for a given shape; the lanes per particle
+                               set the order of a particle's force sums (rounding-level effect) */
 } ldpm_options;
 
 /* Create a specimen from raw geometry (copied).  Validates the mesh rules, derives facet frames,
@@ -204,6 +207,30 @@ int ldpm_load_checkpoint(ldpm_t h, const void *buf);
  * caller.  The result equals the W_kin of ldpm_energy for the same velocities and masses up to
  * summation order.  Errors: INVALID_ARG (NULL pointer, n_dof < 0, n_dof over the limit), CUDA. */
 int ldpm_kinetic_energy_noalloc(const double *v, const double *mass, int64_t n_dof, double *out, void *stream);
+
+/* ---- Batches: many specimens (e.g. random realizations of uneven size) stepped together, one
+ * facet-pass launch and one particle-pass launch per step for all of them.  Each specimen keeps its
+ * own geometry, material, time step, boundary conditions and energies; all share the precision, the
+ * stream and the step counter.  opts[0] supplies precision, stream, graph chunk, device and
+ * autotune.  ldpm_step / ldpm_get_state / ldpm_metrics / checkpoints act on the whole batch (arrays
+ * of all specimens concatenated in index order); ldpm_set_state, ldpm_set_bc and ldpm_energy need a
+ * single-specimen handle (LDPM_E_INVALID_ARG otherwise).  The paper runs one specimen per solver
+ * run; batching is a library service. */
+int ldpm_batch_create(int32_t n, const ldpm_geometry *geoms, const ldpm_material *mats, const ldpm_options *opts,
+                      ldpm_t *out);
+int ldpm_batch_step(ldpm_t h, int64_t nsteps);  /* same as ldpm_step */
+int32_t ldpm_batch_size(ldpm_t h);              /* number of specimens (or a negative error) */
+/* State, energies (as ldpm_energy), metrics (as ldpm_metrics) and sizes/time step (as ldpm_info) of
+ * specimen idx, in that specimen's own particle and facet order. */
+int ldpm_batch_get_state(ldpm_t h, int32_t idx, double *q, double *v, double *hist5, int64_t *step);
+int ldpm_batch_energy(ldpm_t h, int32_t idx, double out[4], double reaction[12]);
+int ldpm_batch_metrics(ldpm_t h, int32_t idx, double *crack_opening, double *tet_volumetric_strain);
+int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt);
+
+/* Launch shape in use: shape[0] tetrahedra per facet-pass block, shape[1] lanes per particle in the
+ * particle pass (set by defaults, the LDPM_TETS_PER_BLOCK / LDPM_GATHER_LANES environment variables
+ * at create, or the autotuner).  Library service; no counterpart in the paper. */
+int ldpm_launch_shape(ldpm_t h, int32_t shape[2]);
 
 /* Release everything the handle owns (synchronises first).  NULL is a no-op. */
 void ldpm_destroy(ldpm_t h);

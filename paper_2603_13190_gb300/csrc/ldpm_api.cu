@@ -571,6 +571,69 @@ int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
 }
 
 int kick(ldpm_ctx *h);
+int enqueue_direct(ldpm_ctx *h, int64_t nsteps);
+
+// Launch-shape autotuner: times each candidate (tetrahedra per facet-pass block x lanes per particle)
+// on the model itself for a few steps, restoring the complete mutable state after every trial, and
+// keeps the fastest.  Results stay deterministic for the chosen shape: the facet-pass shape does not
+// change any arithmetic, the lanes per particle change the order of a particle's sums (rounding-level
+// differences between shapes).
+int autotune(ldpm_ctx *h)
+{
+    DeviceModel &dm = h->dm;
+    const size_t n_ps = 16 * (size_t)dm.N * 8, n_pd = 8 * (size_t)dm.N * 8, n_pm = dm.pm32 ? (size_t)kMirror * dm.N * 4 : 0;
+    const size_t n_h = 12 * (size_t)dm.T * h->r4size();
+    char *bk = nullptr;
+    int rc;
+    if ((rc = dalloc(&bk, n_ps + n_pd + n_pm + n_h + 16))) return rc;
+    auto save = [&](bool to_backup) -> cudaError_t {
+        char *b = bk;
+        void *dst[5] = {b, b + n_ps, b + n_ps + n_pd, b + n_ps + n_pd + n_pm, b + n_ps + n_pd + n_pm + n_h};
+        void *src[5] = {dm.pstate, dm.pdyn, dm.pm32, dm.hist, dm.step};
+        const size_t sz[5] = {n_ps, n_pd, n_pm, n_h, 8};
+        for (int k = 0; k < 5; ++k) {
+            if (!sz[k] || !src[k]) continue;
+            cudaError_t e = to_backup ? cudaMemcpyAsync(dst[k], src[k], sz[k], cudaMemcpyDeviceToDevice, h->stream)
+                                      : cudaMemcpyAsync(src[k], dst[k], sz[k], cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    };
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    const int tets[3] = {8, 16, 32}, lanes[2] = {8, 16};
+    float best = 1e30f;
+    int bt = dm.tets_per_block, bl = dm.gather_lanes;
+    cudaError_t e = save(true);
+    for (int ti = 0; ti < 3 && e == cudaSuccess && rc == 0; ++ti)
+        for (int li = 0; li < 2 && e == cudaSuccess && rc == 0; ++li) {
+            dm.tets_per_block = tets[ti];
+            dm.gather_lanes = lanes[li];
+            if ((rc = enqueue_direct(h, 1))) break;  // warm-up
+            e = cudaEventRecord(a, h->stream);
+            if (e == cudaSuccess && !(rc = enqueue_direct(h, 3))) e = cudaEventRecord(b, h->stream);
+            if (e == cudaSuccess) e = cudaEventSynchronize(b);
+            float ms = 0;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+            if (e == cudaSuccess && ms < best) {
+                best = ms;
+                bt = tets[ti];
+                bl = lanes[li];
+            }
+            if (e == cudaSuccess) e = save(false);
+        }
+    dm.tets_per_block = bt;
+    dm.gather_lanes = bl;
+    cudaError_t e2 = cudaStreamSynchronize(h->stream);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(bk);
+    if (rc) return rc;
+    if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(LDPM_E_CUDA, "autotune: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    return LDPM_OK;
+}
 
 int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, const ldpm_options *opts,
                  ldpm_t *out)
@@ -583,7 +646,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         return fail(LDPM_E_INVALID_ARG, "precision must be LDPM_FP64 or LDPM_MIXED");
     for (int s = 0; s < n; ++s) {
         if (opts[s].precision != o0.precision) return fail(LDPM_E_INVALID_ARG, "specimens must share the precision");
-        if (opts[s].reserved != 0) return fail(LDPM_E_INVALID_ARG, "options.reserved must be 0");
+        if (opts[s].autotune != 0 && opts[s].autotune != 1) return fail(LDPM_E_INVALID_ARG, "options.autotune must be 0 or 1");
         if (!std::isfinite(opts[s].dt) || !std::isfinite(opts[s].ramp_time))
             return fail(LDPM_E_INVALID_ARG, "dt and ramp_time must be finite");
         int rc = check_material(mats[s]);
@@ -740,6 +803,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     }
     // the library keeps the drifted state between calls: first half kick and drift of step 0
     if ((rc = kick(raw))) return rc;
+    if (o0.autotune && (rc = autotune(raw))) return rc;
     CU(cudaDeviceSynchronize());
     guard.armed = false;
     *out = h.release();
@@ -930,10 +994,8 @@ int ldpm_sync(ldpm_t h)
     return check_flag(h);
 }
 
-int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
+static int get_state_range(ldpm_t h, int s_lo, int s_hi, double *q, double *v, double *hist5, int64_t *step)
 {
-    g_err.clear();
-    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
     DevGuard dg(h->device);
     try {
         std::vector<double> ps, h5;
@@ -953,7 +1015,8 @@ int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
         int64_t st = 0;
         CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
         size_t base_p = 0, base_f = 0;
-        for (auto &S : h->sp) {
+        for (int si = s_lo; si < s_hi; ++si) {
+            const SpecHost &S = h->sp[si];
             for (int32_t i = 0; i < S.N; ++i) {
                 const size_t P = (size_t)S.p0 + S.inv_p[i];
                 for (int k = 0; k < 6; ++k) {
@@ -982,10 +1045,18 @@ int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
     }
 }
 
+int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    return get_state_range(h, 0, (int)h->sp.size(), q, v, hist5, step);
+}
+
 int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *hist5, int64_t step)
 {
     g_err.clear();
     if (!h || !q || !v) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL q/v");
+    if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "ldpm_set_state applies to single-specimen handles");
     DevGuard dg(h->device);
     try {
         std::vector<double> ps;
@@ -1068,6 +1139,7 @@ int ldpm_energy(ldpm_t h, double out[4], double reaction[12])
 {
     g_err.clear();
     if (!h || !out) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL out");
+    if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "batch handle: use ldpm_batch_energy");
     DevGuard dg(h->device);
     int rc = energy_of(h, 0, out, reaction);
     if (rc) return rc;
@@ -1120,10 +1192,8 @@ int ldpm_facet_forces(ldpm_t h, double *F3, double *f6)
     }
 }
 
-int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain)
+static int metrics_range(ldpm_t h, int s_lo, int s_hi, double *crack_opening, double *tet_volumetric_strain)
 {
-    g_err.clear();
-    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
     DevGuard dg(h->device);
     try {
         int rc = launch_facet_any(h, FACET_METRIC, nullptr);
@@ -1142,7 +1212,8 @@ int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain)
             CU(cudaMemcpy(fo.data(), h->dm.fout, Fint * 4 * sizeof(double), cudaMemcpyDeviceToHost));
         }
         size_t base_f = 0, base_t = 0;
-        for (auto &S : h->sp) {
+        for (int si = s_lo; si < s_hi; ++si) {
+            const SpecHost &S = h->sp[si];
             if (crack_opening)
                 for (int32_t k = 0; k < S.F; ++k) crack_opening[base_f + k] = fo[4 * (size_t)S.fmap[k]];
             if (tet_volumetric_strain)
@@ -1154,6 +1225,13 @@ int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain)
     } catch (const std::bad_alloc &) {
         return fail(LDPM_E_OOM, "host allocation failed");
     }
+}
+
+int ldpm_metrics(ldpm_t h, double *crack_opening, double *tet_volumetric_strain)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    return metrics_range(h, 0, (int)h->sp.size(), crack_opening, tet_volumetric_strain);
 }
 
 int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_time)
@@ -1293,6 +1371,82 @@ int ldpm_load_checkpoint(ldpm_t h, const void *buf)
     for (size_t s = 0; s < h->sp.size(); ++s) std::memcpy(&h->sp[s].W_kin0, q + 16 + 8 * s, 8);
     CU(launch_mirror(h->dm, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    return LDPM_OK;
+}
+
+int ldpm_batch_create(int32_t n, const ldpm_geometry *geoms, const ldpm_material *mats, const ldpm_options *opts,
+                      ldpm_t *out)
+{
+    g_err.clear();
+    if (n < 1 || !geoms || !mats || !opts) return fail(LDPM_E_INVALID_ARG, "need n >= 1 and non-NULL arrays");
+    try {
+        return create_model(n, geoms, mats, opts, out);
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(LDPM_E_CUDA, "unexpected exception in ldpm_batch_create");
+    }
+}
+
+int ldpm_batch_step(ldpm_t h, int64_t nsteps) { return ldpm_step(h, nsteps); }
+
+int32_t ldpm_batch_size(ldpm_t h)
+{
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    return (int32_t)h->sp.size();
+}
+
+int ldpm_batch_get_state(ldpm_t h, int32_t idx, double *q, double *v, double *hist5, int64_t *step)
+{
+    g_err.clear();
+    if (!h || idx < 0 || idx >= (int32_t)h->sp.size()) return fail(LDPM_E_INVALID_ARG, "bad handle or index");
+    return get_state_range(h, idx, idx + 1, q, v, hist5, step);
+}
+
+int ldpm_batch_energy(ldpm_t h, int32_t idx, double out[4], double reaction[12])
+{
+    g_err.clear();
+    if (!h || !out || idx < 0 || idx >= (int32_t)h->sp.size())
+        return fail(LDPM_E_INVALID_ARG, "bad handle, index or NULL out");
+    DevGuard dg(h->device);
+    int rc = energy_of(h, idx, out, reaction);
+    if (rc) return rc;
+    return check_flag(h);
+}
+
+int ldpm_batch_metrics(ldpm_t h, int32_t idx, double *crack_opening, double *tet_volumetric_strain)
+{
+    g_err.clear();
+    if (!h || idx < 0 || idx >= (int32_t)h->sp.size()) return fail(LDPM_E_INVALID_ARG, "bad handle or index");
+    return metrics_range(h, idx, idx + 1, crack_opening, tet_volumetric_strain);
+}
+
+int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt)
+{
+    g_err.clear();
+    if (!h || idx < 0 || idx >= (int32_t)h->sp.size()) return fail(LDPM_E_INVALID_ARG, "bad handle or index");
+    DevGuard dg(h->device);
+    const SpecHost &S = h->sp[idx];
+    if (info) {
+        CU(cudaStreamSynchronize(h->stream));
+        int64_t st = 0;
+        CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
+        info[0] = S.N;
+        info[1] = S.T;
+        info[2] = S.F;
+        info[3] = h->prec;
+        info[4] = st;
+    }
+    if (dt) *dt = S.dt;
+    return LDPM_OK;
+}
+
+int ldpm_launch_shape(ldpm_t h, int32_t shape[2])
+{
+    g_err.clear();
+    if (!h || !shape) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL shape");
+    shape[0] = h->dm.tets_per_block;
+    shape[1] = h->dm.gather_lanes;
     return LDPM_OK;
 }
 

@@ -48,7 +48,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("graph_chunk", C.c_int32), ("dt", C.c_double), ("dt_factor", C.c_double),
                 ("cuda_stream", C.c_void_p), ("bc_mask", C.c_void_p), ("bc_vel", C.c_void_p),
                 ("ramp_time", C.c_double), ("v0", C.c_void_p), ("f_ext", C.c_void_p), ("device", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("autotune", C.c_int32)]
 
 
 _lib = None
@@ -87,6 +87,14 @@ def lib():
             "ldpm_destroy": ([P], None),
             "ldpm_last_error": ([], C.c_char_p),
             "ldpm_kinetic_energy_noalloc": ([P, P, I64, P, P], C.c_int),
+            "ldpm_batch_create": ([I32, P, P, P, P], C.c_int),
+            "ldpm_batch_step": ([P, I64], C.c_int),
+            "ldpm_batch_size": ([P], I32),
+            "ldpm_batch_get_state": ([P, I32, P, P, P, P], C.c_int),
+            "ldpm_batch_energy": ([P, I32, P, P], C.c_int),
+            "ldpm_batch_metrics": ([P, I32, P, P], C.c_int),
+            "ldpm_batch_info": ([P, I32, P, P], C.c_int),
+            "ldpm_launch_shape": ([P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -116,13 +124,8 @@ def _stream_handle(stream) -> int | None:
 # --------------------------------------------------------------------------------------------------
 # Entry points with the C names.
 # --------------------------------------------------------------------------------------------------
-def ldpm_create(spec, material: dict, precision: int = LDPM_MIXED, dt: float = 0.0, dt_factor: float = 0.9,
-                bc=None, f_ext=None, stream=None, graph_chunk: int = 0, mass=None, inertia=None,
-                device: int = -1):
-    """Create a handle from a specimen (see specimen.Specimen) and a material dict.  Returns (handle,
-    keepalive) -- the caller-owned arrays only need to live for the duration of the call."""
-    keep = []
-
+def _structs(spec, material: dict, precision: int, dt: float, dt_factor: float, bc, f_ext, stream, graph_chunk,
+             mass, inertia, device, autotune, keep):
     def arr(a, dtp):
         if a is None:
             return None
@@ -143,15 +146,90 @@ def ldpm_create(spec, material: dict, precision: int = LDPM_MIXED, dt: float = 0
     o.dt_factor = float(dt_factor)
     o.cuda_stream = _stream_handle(stream)
     o.device = int(device)
+    o.autotune = 1 if autotune else 0
     if bc is not None:
         o.bc_mask = _ptr(arr(bc.mask, np.int32))
         o.bc_vel = _ptr(arr(bc.vel, np.float64))
         o.ramp_time = float(bc.ramp_time)
         o.v0 = _ptr(arr(bc.v0, np.float64))
     o.f_ext = _ptr(arr(f_ext, np.float64))
+    return g, m, o
+
+
+def ldpm_create(spec, material: dict, precision: int = LDPM_MIXED, dt: float = 0.0, dt_factor: float = 0.9,
+                bc=None, f_ext=None, stream=None, graph_chunk: int = 0, mass=None, inertia=None,
+                device: int = -1, autotune: bool = False):
+    """Create a handle from a specimen (see specimen.Specimen) and a material dict.  The caller-owned
+    arrays only need to live for the duration of the call."""
+    keep = []
+    g, m, o = _structs(spec, material, precision, dt, dt_factor, bc, f_ext, stream, graph_chunk, mass, inertia,
+                       device, autotune, keep)
     h = C.c_void_p()
     _check(lib().ldpm_create(C.byref(g), C.byref(m), C.byref(o), C.byref(h)), "ldpm_create")
     return h
+
+
+def ldpm_batch_create(specs, materials, precision: int = LDPM_MIXED, dts=None, bcs=None, stream=None,
+                      graph_chunk: int = 0, device: int = -1, autotune: bool = False, dt_factor: float = 0.9):
+    """Create one handle stepping all specimens together (lists of equal length)."""
+    n = len(specs)
+    keep = []
+    G, M, O = (Geometry * n)(), (Material * n)(), (Options * n)()
+    for i, sp in enumerate(specs):
+        g, m, o = _structs(sp, materials[i], precision, 0.0 if dts is None else dts[i], dt_factor,
+                           None if bcs is None else bcs[i], None, stream, graph_chunk, None, None, device,
+                           autotune, keep)
+        G[i], M[i], O[i] = g, m, o
+    h = C.c_void_p()
+    _check(lib().ldpm_batch_create(n, G, M, O, C.byref(h)), "ldpm_batch_create")
+    return h
+
+
+def ldpm_batch_step(h, nsteps: int) -> None:
+    _check(lib().ldpm_batch_step(h, int(nsteps)), "ldpm_batch_step")
+
+
+def ldpm_batch_size(h) -> int:
+    n = lib().ldpm_batch_size(h)
+    if n < 0:
+        _check(n, "ldpm_batch_size")
+    return int(n)
+
+
+def ldpm_batch_get_state(h, idx: int, N: int, F: int, hist: bool = True):
+    q = np.zeros((N, 6))
+    v = np.zeros((N, 6))
+    h5 = np.zeros((F, 5)) if hist else None
+    st = C.c_int64(0)
+    _check(lib().ldpm_batch_get_state(h, int(idx), _ptr(q), _ptr(v), _ptr(h5), C.byref(st)), "ldpm_batch_get_state")
+    return q, v, h5, st.value
+
+
+def ldpm_batch_energy(h, idx: int):
+    out = np.zeros(4)
+    r = np.zeros(12)
+    _check(lib().ldpm_batch_energy(h, int(idx), _ptr(out), _ptr(r)), "ldpm_batch_energy")
+    return out, r
+
+
+def ldpm_batch_metrics(h, idx: int, F: int, T: int):
+    w = np.zeros(F)
+    eV = np.zeros(T)
+    _check(lib().ldpm_batch_metrics(h, int(idx), _ptr(w), _ptr(eV)), "ldpm_batch_metrics")
+    return w, eV
+
+
+def ldpm_batch_info(h, idx: int):
+    info = np.zeros(5, np.int64)
+    dt = C.c_double(0.0)
+    _check(lib().ldpm_batch_info(h, int(idx), _ptr(info), C.byref(dt)), "ldpm_batch_info")
+    return info, dt.value
+
+
+def ldpm_launch_shape(h):
+    shape = np.zeros(2, np.int32)
+    _check(lib().ldpm_launch_shape(h, _ptr(shape)), "ldpm_launch_shape")
+    return int(shape[0]), int(shape[1])
 
 
 def ldpm_step(h, nsteps: int) -> None:
@@ -260,6 +338,46 @@ def ldpm_last_error() -> str:
 # --------------------------------------------------------------------------------------------------
 # Convenience object (still marshalling only).
 # --------------------------------------------------------------------------------------------------
+class Batch:
+    """Several specimens stepped together on the GPU."""
+
+    def __init__(self, specs, materials, precision: str | int = "mixed", dts=None, bcs=None, **kw):
+        prec = precision if isinstance(precision, int) else (LDPM_MIXED if precision == "mixed" else LDPM_FP64)
+        self.sizes = [(s.n_particles, s.n_tets, s.n_facets) for s in specs]
+        self.h = ldpm_batch_create(specs, materials, prec, dts=dts, bcs=bcs, **kw)
+
+    def __del__(self):
+        self.close()
+
+    def close(self):
+        if getattr(self, "h", None):
+            ldpm_destroy(self.h)
+            self.h = None
+
+    def __len__(self):
+        return len(self.sizes)
+
+    def step(self, n: int = 1):
+        ldpm_batch_step(self.h, n)
+
+    def get_state(self, idx: int, hist: bool = True):
+        N, _, F = self.sizes[idx]
+        return ldpm_batch_get_state(self.h, idx, N, F, hist)
+
+    def energy(self, idx: int):
+        return ldpm_batch_energy(self.h, idx)
+
+    def metrics(self, idx: int):
+        _, T, F = self.sizes[idx]
+        return ldpm_batch_metrics(self.h, idx, F, T)
+
+    def info(self, idx: int):
+        return ldpm_batch_info(self.h, idx)
+
+    def launch_shape(self):
+        return ldpm_launch_shape(self.h)
+
+
 class Model:
     """One specimen on the GPU.  Arrays are in the specimen's own particle/facet order."""
 
@@ -300,6 +418,9 @@ class Model:
 
     def metrics(self):
         return ldpm_metrics(self.h, self.F, self.T)
+
+    def launch_shape(self):
+        return ldpm_launch_shape(self.h)
 
     def info(self):
         return ldpm_info(self.h)

@@ -8,7 +8,10 @@ seeded synthetic cube that stands in for one of the paper's benchmark families (
   * uniaxial_tension   -- tensile fracture to softening (dog-bone test, Sec. 4.3), 50 mm cube,
                           ~1.8M facets, FP32 facets / FP64 particle state;
   * confined_compression -- hydrostatic + triaxial compression with strain hardening (uniaxial-strain
-                          test, Sec. 4.2), 100 mm cube, ~12.5M facets, mixed precision.
+                          test, Sec. 4.2), 100 mm cube, ~12.5M facets, mixed precision;
+  * batched_unconfined_compression -- 64 random cubes of edge U(30, 60) mm, d = 2..4 mm, unconfined
+                          compression between frictionless ("free") platens (Sec. 4.5), stepped as one
+                          batch; particle counts scale with volume from uniaxial_tension's density.
 
 Boundary-condition codes per degree of freedom (u_x, u_y, u_z, theta_x, theta_y, theta_z):
   0 = free, 1 = fixed (velocity 0), 2 = prescribed velocity bc_vel * ramp(t),
@@ -138,6 +141,52 @@ def confined_compression_bc(spec: Specimen, velocity: float = 25.0, phase: int =
     return bc
 
 
+def unconfined_compression_bc(spec: Specimen, velocity: float = 50.0, ramp_time: float = 2e-4) -> BoundaryConditions:
+    """Unconfined compression with free platens as in Sec. 4.5: on the top and bottom faces u_z is
+    prescribed (top moving down at `velocity`, bottom held) and theta_x, theta_y are fixed, while u_x,
+    u_y and theta_z stay free; the node nearest each platen centre also holds u_x, u_y, theta_z."""
+    bc = free_bc(spec.n_particles)
+    bot, top = spec.face_nodes(2, 0), spec.face_nodes(2, 1)
+    for nodes in (bot, top):
+        bc.mask[np.ix_(nodes, [3, 4])] = FIXED
+        c = nodes[np.argmin(np.linalg.norm(spec.x[nodes, :2] - 0.5 * spec.edge, axis=1))]
+        bc.mask[c, [0, 1, 5]] = FIXED
+    bc.mask[bot, 2] = FIXED
+    bc.mask[top, 2] = PRESCRIBED
+    bc.vel[top, 2] = -velocity
+    bc.ramp_time = ramp_time
+    return bc
+
+
+# Batched workload: n cubes, edges uniform in [30, 60] mm (seeded), particle count at the density of
+# uniaxial_tension (25000 particles in a 50 mm cube).
+BATCH_DENSITY = 25000.0 / 50.0 ** 3
+
+
+def batch_recipe(n: int = 64, seed: int = 1):
+    rng = np.random.default_rng(seed)
+    edges = rng.uniform(30.0, 60.0, n)
+    return [(float(L), 2.0, 4.0, int(round(BATCH_DENSITY * L ** 3)), seed * 1000 + i) for i, L in enumerate(edges)]
+
+
+def _make(args):
+    L, dmin, dmax, n, sd = args
+    return make_cube_specimen(L, dmin, dmax, n, sd)
+
+
+def batch_specimens(n: int = 64, seed: int = 1, processes: int | None = None):
+    """Generate the batch in parallel worker processes (spawned, so no CUDA context is inherited)."""
+    import multiprocessing as mp
+    import os as _os
+
+    recipe = batch_recipe(n, seed)
+    procs = processes or max(1, min(len(recipe), (_os.cpu_count() or 2)))
+    if procs == 1:
+        return [_make(r) for r in recipe]
+    with mp.get_context("spawn").Pool(procs) as pool:
+        return pool.map(_make, recipe)
+
+
 WORKLOADS = {
     "elastic_vibration": Workload("elastic_vibration", 25.0, 4.0, 8.0, 420, 1, dict(WORKLOAD_MATERIAL, elastic=1),
                                   "fp64", 2000),
@@ -146,6 +195,8 @@ WORKLOADS = {
     "confined_compression": Workload("confined_compression", 100.0, 3.0, 6.0, 165000, 1,
                                      dict(WORKLOAD_MATERIAL), "mixed", 50000),
 }
+# (the batched workload is built by batch_specimens / batch_recipe; material WORKLOAD_MATERIAL with
+# the friction of the workload definition: mu_0 = 0.2, mu_inf = 0, sigma_N0 = 600 MPa)
 
 
 def workload_bc(name: str, spec: Specimen) -> BoundaryConditions:
@@ -155,4 +206,6 @@ def workload_bc(name: str, spec: Specimen) -> BoundaryConditions:
         return uniaxial_tension_bc(spec)
     if name == "confined_compression":
         return confined_compression_bc(spec)
+    if name == "batched_unconfined_compression":
+        return unconfined_compression_bc(spec)
     raise KeyError(name)

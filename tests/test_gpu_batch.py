@@ -1,0 +1,85 @@
+"""Batched stepping: several uneven specimens in one launch per pass equal their separate runs."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_13190_gb300 import ldpm, specimen, workloads
+from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
+
+pytestmark = pytest.mark.gpu
+MAT = dict(WORKLOAD_MATERIAL)
+
+
+def nrel(a, b):
+    den = np.abs(b).max()
+    return float(np.abs(a - b).max() / den) if den > 0 else float(np.abs(a - b).max())
+
+
+@pytest.fixture(scope="module")
+def trio():
+    specs = [specimen.make_cube_specimen(L, 2.0, 4.0, n, seed=s) for L, n, s in ((9.0, 110, 31), (14.0, 420, 32),
+                                                                                  (11.0, 230, 33))]
+    bcs = [workloads.unconfined_compression_bc(specs[0], velocity=300.0, ramp_time=1e-5),
+           workloads.uniaxial_tension_bc(specs[1], velocity=150.0, ramp_time=1e-5),
+           workloads.confined_compression_bc(specs[2], velocity=300.0, ramp_time=1e-5)]
+    mats = [MAT, dict(MAT, sigma_t=3.5), dict(MAT, E0=40000.0)]
+    dts = [0.85 * oracle.Oracle(s, m, 1e-7, b).critical_dt() for s, m, b in zip(specs, mats, bcs)]
+    return specs, bcs, mats, dts
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_equals_single_runs_bitwise(trio, prec):
+    specs, bcs, mats, dts = trio
+    b = ldpm.Batch(specs, mats, prec, dts=dts, bcs=bcs)
+    assert len(b) == 3
+    b.step(120)
+    for i, (s, m_, bc, dt) in enumerate(zip(specs, mats, bcs, dts)):
+        single = ldpm.Model(s, m_, precision=prec, dt=dt, bc=bc)
+        single.step(120)
+        sb, ss = b.get_state(i), single.get_state()
+        for x, y in zip(sb[:3], ss[:3]):
+            assert np.array_equal(x, y)
+        eb, rb = b.energy(i)
+        es, rs = single.energy()
+        assert np.array_equal(eb, es) and np.array_equal(rb, rs)
+        info, dti = b.info(i)
+        assert info[0] == s.n_particles and info[2] == s.n_facets and dti == dt
+        single.close()
+
+
+def test_batch_matches_each_oracle_fp64(trio):
+    specs, bcs, mats, dts = trio
+    b = ldpm.Batch(specs, mats, "fp64", dts=dts, bcs=bcs)
+    b.step(80)
+    for i, (s, m_, bc, dt) in enumerate(zip(specs, mats, bcs, dts)):
+        o = oracle.Oracle(s, m_, dt, bc)
+        o.step(80)
+        qg, vg, hg, _ = b.get_state(i)
+        qo, vo, ho, _ = o.get_state()
+        assert nrel(qg, qo) <= 1e-10 and nrel(vg, vo) <= 1e-10 and nrel(hg, ho) <= 1e-10
+        wg, eVg = b.metrics(i)
+        wo, eVo = o.metrics()
+        assert nrel(eVg, eVo) <= 1e-10
+
+
+def test_autotuned_batch_stays_within_rounding(trio):
+    specs, bcs, mats, dts = trio
+    a = ldpm.Batch(specs, mats, "mixed", dts=dts, bcs=bcs, autotune=True)
+    d = ldpm.Batch(specs, mats, "mixed", dts=dts, bcs=bcs)
+    tets, lanes = a.launch_shape()
+    assert tets in (8, 16, 32) and lanes in (8, 16)
+    a.step(60)
+    d.step(60)
+    for i in range(3):
+        qa, va, _, _ = a.get_state(i)
+        qd, vd, _, _ = d.get_state(i)
+        assert nrel(qa, qd) <= 1e-6 and nrel(va, vd) <= 1e-4
+
+
+def test_batch_rejects_single_specimen_calls(trio):
+    specs, bcs, mats, dts = trio
+    b = ldpm.Batch(specs[:2], mats[:2], "mixed", dts=dts[:2], bcs=bcs[:2])
+    with pytest.raises(ldpm.LdpmError):
+        ldpm.ldpm_energy(b.h)
+    with pytest.raises(ldpm.LdpmError):
+        ldpm.ldpm_set_bc(b.h, bcs[0].mask, bcs[0].vel, 0.0)
