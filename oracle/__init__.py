@@ -1,4 +1,4 @@
-"""ctypes wrapper of the FP64 CPU oracle (ldpm_oracle.c).
+"""ctypes wrapper of the FP64 CPU oracle (ldpm_oracle.cpp).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the benchmark's CPU-baseline
 and reference legs.  The product path (the CUDA library and its binding) never imports this.
@@ -12,7 +12,7 @@ import subprocess
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-_SRC = os.path.join(_HERE, "ldpm_oracle.c")
+_SRC = os.path.join(_HERE, "ldpm_oracle.cpp")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 
 MATERIAL_FIELDS = ("rho", "E0", "alpha", "sigma_t", "l_t", "r_st", "n_t", "sigma_c0", "Hc0_E0", "Hc1_E0",
@@ -24,11 +24,11 @@ class OrcMaterial(C.Structure):
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain -O2, no FMA contraction, no fast-math)."""
+    """Compile the oracle with g++ (plain -O2, no FMA contraction, no fast-math)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp.%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
                                "-shared", _SRC, "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -60,6 +60,10 @@ def lib():
         L.orc_facet_march.argtypes = [C.POINTER(OrcMaterial), D, I64, P, P, P, P]
         L.orc_metrics.argtypes = [P, P, P]
         L.orc_set_bc.argtypes = [P, P, P, D]
+        L.orc_set_facet_params.argtypes = [P, P, P, P]
+        L.orc_tangent.argtypes = [P, I64, P, I32, P, P, P, P, P]
+        L.orc_tangent.restype = C.c_int
+        L.orc_facet_law_jacobian.argtypes = [C.POINTER(OrcMaterial), D, P, P, P]
         _lib = L
     return _lib
 
@@ -87,6 +91,20 @@ def facet_law(mat: dict, l, e, de, eV, t_old, emax_old):
     lib().orc_facet_law(C.byref(m), float(l), _p(e), _p(de), float(eV), _p(t_old), float(emax_old), _p(t_new),
                         C.byref(em))
     return t_new, em.value
+
+
+LAW_INPUTS = ("eN", "eM", "eL", "deN", "deM", "deL", "eV", "tN", "tM", "tL", "emax", "E0", "alpha", "sigma_t")
+
+
+def facet_law_jacobian(mat: dict, l, x):
+    """Constitutive update and its Jacobian at x = (e[3], de[3], eV, t_old[3], e_max_old, E0, alpha,
+    sigma_t) (the order of LAW_INPUTS): returns (out[4] = t_new[3], e_max_new; jac[4, 14])."""
+    m = material_struct(mat)
+    x = np.ascontiguousarray(x, np.float64).reshape(14)
+    out = np.zeros(4)
+    jac = np.zeros((4, 14))
+    lib().orc_facet_law_jacobian(C.byref(m), float(l), _p(x), _p(out), _p(jac))
+    return out, jac
 
 
 def facet_march(mat: dict, l, path, eV):
@@ -203,6 +221,29 @@ class Oracle:
         vel = np.ascontiguousarray(bc.vel, np.float64)
         self._keep += [mask, vel]
         lib().orc_set_bc(self.h, _p(mask), _p(vel), float(bc.ramp_time))
+
+    def set_facet_params(self, E0=None, alpha=None, sigma_t=None) -> None:
+        """Per-facet E0, alpha, sigma_t ([F] each, specimen facet order); None = material value."""
+        arrs = [None if a is None else np.ascontiguousarray(np.broadcast_to(a, (self.F,)), np.float64)
+                for a in (E0, alpha, sigma_t)]
+        lib().orc_set_facet_params(self.h, *[_p(a) for a in arrs])
+
+    def tangent(self, nsteps: int, seed, dE0=None, dalpha=None, dsigma_t=None):
+        """J = time mean over the next `nsteps` steps of sum_i seed_i R_i (seed [N, 6], reactions on
+        constrained DOFs), and its derivatives along the rows of dE0 / dalpha / dsigma_t ([nd, F] each,
+        None = 0).  The model's state is left unchanged.  Returns (J, dJ[nd])."""
+        seed = np.ascontiguousarray(seed, np.float64).reshape(self.N, 6)
+        dirs = [None if d is None else np.ascontiguousarray(np.atleast_2d(d), np.float64) for d in (dE0, dalpha, dsigma_t)]
+        nd = max([0] + [d.shape[0] for d in dirs if d is not None])
+        for d in dirs:
+            if d is not None and d.shape != (nd, self.F):
+                raise ValueError("direction arrays must be [nd, F]")
+        J = C.c_double(0.0)
+        dJ = np.zeros(nd)
+        rc = lib().orc_tangent(self.h, int(nsteps), _p(seed), nd, *[_p(d) for d in dirs], C.byref(J), _p(dJ))
+        if rc != 0:
+            raise FloatingPointError("oracle trajectory became non-finite")
+        return J.value, dJ
 
     def geometry(self):
         n = np.zeros((self.F, 3))

@@ -1,5 +1,6 @@
 /*
- * ldpm_oracle.c -- plain, slow FP64 reference of one LDPM explicit central-difference step.
+ * ldpm_oracle.cpp -- plain, slow FP64 reference of one LDPM explicit central-difference step, and
+ * the exact derivative of the same computation with respect to per-facet material parameters.
  *
  * TEST INFRASTRUCTURE ONLY.  Only the tests, the smoke check and the CPU-baseline leg of the
  * benchmark load this library.  It shares no code, header or table with the CUDA library; both
@@ -30,15 +31,110 @@
  *   - in the fracture branch an effective strain below 1e-150 (where t/e is 0/0 in floating point)
  *     takes the elastic limit t = E e;
  *   - k_t > 0 (tensile reloading), E_d != E0 and r_s != 0 are outside what is pinned here.
+ *
+ * Derivatives (the paper has none; they serve the adjoint of the explicit step).  The law and the
+ * step are templates over the scalar type.  Instantiated with `double` they are the reference step;
+ * instantiated with a forward-mode dual number they carry, next to every value, its derivative along
+ * given directions of the per-facet parameters (E0, alpha, sigma_t), through every operation of the
+ * same code.  Where an operation is not differentiable (sqrt at 0, a max or clamp at its switch
+ * point, |x| at 0) the derivative of the branch the value takes is used, and sqrt'(0) is taken as 0.
  */
 #include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <type_traits>
+#include <vector>
 
 #define ORC_PI 3.14159265358979323846
 /* effective strains below this are treated as zero in the fracture law (squares would underflow) */
 #define ORC_TINY_STRAIN 1e-150
-#include <stdint.h>
-#include <stdlib.h>
-#include <string.h>
+
+/* ------------------------------------------------------------------------------------------ */
+/* Forward-mode dual number: value v and its derivatives d[0..D) along D directions.             */
+/* ------------------------------------------------------------------------------------------ */
+template <int D>
+struct Dual {
+    double v;
+    double d[D];
+    Dual() : v(0.0) { for (int i = 0; i < D; ++i) d[i] = 0.0; }
+    Dual(double x) : v(x) { for (int i = 0; i < D; ++i) d[i] = 0.0; }
+};
+template <int D> Dual<D> operator+(const Dual<D> &a, const Dual<D> &b) { Dual<D> r(a.v + b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] + b.d[i]; return r; }
+template <int D> Dual<D> operator-(const Dual<D> &a, const Dual<D> &b) { Dual<D> r(a.v - b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] - b.d[i]; return r; }
+template <int D> Dual<D> operator-(const Dual<D> &a) { Dual<D> r(-a.v); for (int i = 0; i < D; ++i) r.d[i] = -a.d[i]; return r; }
+template <int D> Dual<D> operator*(const Dual<D> &a, const Dual<D> &b) { Dual<D> r(a.v * b.v); for (int i = 0; i < D; ++i) r.d[i] = a.d[i] * b.v + a.v * b.d[i]; return r; }
+template <int D> Dual<D> operator/(const Dual<D> &a, const Dual<D> &b)
+{
+    Dual<D> r(a.v / b.v);
+    for (int i = 0; i < D; ++i) r.d[i] = (a.d[i] - r.v * b.d[i]) / b.v; /* (a/b)' = (a' - (a/b) b') / b */
+    return r;
+}
+template <int D> Dual<D> operator+(const Dual<D> &a, double b) { return a + Dual<D>(b); }
+template <int D> Dual<D> operator+(double a, const Dual<D> &b) { return Dual<D>(a) + b; }
+template <int D> Dual<D> operator-(const Dual<D> &a, double b) { return a - Dual<D>(b); }
+template <int D> Dual<D> operator-(double a, const Dual<D> &b) { return Dual<D>(a) - b; }
+template <int D> Dual<D> operator*(const Dual<D> &a, double b) { return a * Dual<D>(b); }
+template <int D> Dual<D> operator*(double a, const Dual<D> &b) { return Dual<D>(a) * b; }
+template <int D> Dual<D> operator/(const Dual<D> &a, double b) { return a / Dual<D>(b); }
+template <int D> Dual<D> operator/(double a, const Dual<D> &b) { return Dual<D>(a) / b; }
+template <int D> Dual<D> &operator+=(Dual<D> &a, const Dual<D> &b) { a = a + b; return a; }
+template <int D> Dual<D> &operator-=(Dual<D> &a, const Dual<D> &b) { a = a - b; return a; }
+template <int D> Dual<D> &operator*=(Dual<D> &a, const Dual<D> &b) { a = a * b; return a; }
+template <int D> Dual<D> &operator/=(Dual<D> &a, const Dual<D> &b) { a = a / b; return a; }
+/* comparisons act on the value */
+template <int D> bool operator<(const Dual<D> &a, const Dual<D> &b) { return a.v < b.v; }
+template <int D> bool operator>(const Dual<D> &a, const Dual<D> &b) { return a.v > b.v; }
+template <int D> bool operator<=(const Dual<D> &a, const Dual<D> &b) { return a.v <= b.v; }
+template <int D> bool operator<(const Dual<D> &a, double b) { return a.v < b; }
+template <int D> bool operator>(const Dual<D> &a, double b) { return a.v > b; }
+template <int D> bool operator<=(const Dual<D> &a, double b) { return a.v <= b; }
+template <int D> Dual<D> sqrt(const Dual<D> &a)
+{
+    Dual<D> r(sqrt(a.v));
+    for (int i = 0; i < D; ++i) r.d[i] = r.v > 0.0 ? a.d[i] / (2.0 * r.v) : 0.0;
+    return r;
+}
+template <int D> Dual<D> exp(const Dual<D> &a)
+{
+    Dual<D> r(exp(a.v));
+    for (int i = 0; i < D; ++i) r.d[i] = r.v * a.d[i];
+    return r;
+}
+template <int D> Dual<D> sin(const Dual<D> &a)
+{
+    Dual<D> r(sin(a.v));
+    const double c = cos(a.v);
+    for (int i = 0; i < D; ++i) r.d[i] = c * a.d[i];
+    return r;
+}
+template <int D> Dual<D> cos(const Dual<D> &a)
+{
+    Dual<D> r(cos(a.v));
+    const double s = sin(a.v);
+    for (int i = 0; i < D; ++i) r.d[i] = -s * a.d[i];
+    return r;
+}
+/* d atan2(y, x) = (x dy - y dx) / (x^2 + y^2) */
+template <int D> Dual<D> atan2(const Dual<D> &y, const Dual<D> &x)
+{
+    Dual<D> r(atan2(y.v, x.v));
+    const double den = x.v * x.v + y.v * y.v;
+    for (int i = 0; i < D; ++i) r.d[i] = den > 0.0 ? (x.v * y.d[i] - y.v * x.d[i]) / den : 0.0;
+    return r;
+}
+template <int D> Dual<D> pow(const Dual<D> &a, double n)
+{
+    Dual<D> r(pow(a.v, n));
+    const double g = n * pow(a.v, n - 1.0);
+    for (int i = 0; i < D; ++i) r.d[i] = g * a.d[i];
+    return r;
+}
+template <int D> Dual<D> fabs(const Dual<D> &a) { return a.v < 0.0 ? -a : a; }
+
+static inline double value_of(double x) { return x; }
+template <int D> static inline double value_of(const Dual<D> &x) { return x.v; }
 
 typedef struct {
     double rho, E0, alpha, sigma_t, l_t, r_st, n_t, sigma_c0, Hc0_E0, Hc1_E0, kc0, kc1, kc2, kc3,
@@ -70,7 +166,39 @@ typedef struct {
     double *e_prev;                 /* [F][3] strain of the current state */
     double *F_facet;                /* [F][3] facet force acting on I: A P t */
     double W_int, W_ext, W_kin0;
+    /* per-facet E0, alpha, sigma_t ([F] each), or null: the material's values for every facet */
+    double *pE0, *palpha, *psig;
 } orc_model;
+
+extern "C" {
+void orc_facet_law(const orc_material *p, double l, const double e[3], const double de[3], double eV,
+                   const double t_old[3], double emax_old, double t_new[3], double *emax_new);
+void orc_facet_law_jacobian(const orc_material *p, double l, const double in[14], double out[4], double jac[56]);
+void orc_destroy(orc_model *M);
+orc_model *orc_create(int32_t N, int32_t T, int32_t F, const double *x, const double *diameter, const int32_t *tet,
+                      const int32_t *fpi, const int32_t *fpj, const int32_t *ftet, const double *fvtx,
+                      const double *mass_in, const double *inertia_in, const orc_material *mat, double dt,
+                      const int32_t *bc_mask, const double *bc_vel, double ramp_time, const double *v0,
+                      const double *f_ext);
+int orc_step(orc_model *M, int64_t nsteps);
+void orc_get_state(const orc_model *M, double *q, double *v, double *hist5, int64_t *step);
+void orc_set_state(orc_model *M, const double *q, const double *v, const double *hist5, int64_t step);
+void orc_energy(const orc_model *M, double out[4], double reaction[12]);
+void orc_facet_forces(const orc_model *M, double *F3, double *f6);
+void orc_strains(const orc_model *M, const double *q, double *e3, double *eV);
+void orc_elastic_force(const orc_model *M, const double *q, double *f6);
+double orc_lambda_max(const orc_model *M, const double *x0, int32_t iters);
+void orc_geometry(const orc_model *M, double *n3, double *len, double *area, double *mass6, double *ci3,
+                  double *cj3);
+int32_t orc_sizes(const orc_model *M, int32_t *NTF);
+void orc_facet_march(const orc_material *p, double l, int64_t n, const double *path, const double *eV,
+                     double *t_out, double *emax_out);
+void orc_metrics(const orc_model *M, double *w, double *eV);
+void orc_set_bc(orc_model *M, const int32_t *mask, const double *vel, double ramp_time);
+void orc_set_facet_params(orc_model *M, const double *E0, const double *alpha, const double *sigma_t);
+int orc_tangent(const orc_model *M, int64_t nsteps, const double *seed, int32_t nd, const double *dE0,
+                const double *dalpha, const double *dsigma_t, double *J, double *dJ);
+}
 
 static void cross3(const double a[3], const double b[3], double c[3])
 {
@@ -96,10 +224,10 @@ static double ramp(const orc_model *M, double t)
 /* the tetrahedron's volumetric strain eV, the facet length l, the previous tractions t_old and */
 /* maximum effective strain.  Outputs the new tractions and e_max.                              */
 /* ------------------------------------------------------------------------------------------ */
-void orc_facet_law(const orc_material *p, double l, const double e[3], const double de[3], double eV,
-                   const double t_old[3], double emax_old, double t_new[3], double *emax_new)
+template <class S>
+static void facet_law(const orc_material *p, S E0, S alpha, S sigma_t, double l, const S e[3], const S de[3],
+                      S eV, const S t_old[3], S emax_old, S t_new[3], S *emax_new)
 {
-    const double E0 = p->E0, alpha = p->alpha;
     *emax_new = emax_old;
     if (p->elastic) {
         /* Sec. 2: t = E e with E = E0 diag(1, alpha, alpha). */
@@ -110,8 +238,8 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
     }
     if (e[0] > 0.0) {
         /* App. A.1, fracture.  Effective strain e = sqrt(e_N^2 + alpha (e_M^2 + e_L^2)). */
-        double eT2 = e[1] * e[1] + e[2] * e[2];
-        double eeff = sqrt(e[0] * e[0] + alpha * eT2);
+        S eT2 = e[1] * e[1] + e[2] * e[2];
+        S eeff = sqrt(e[0] * e[0] + alpha * eT2);
         if (eeff < ORC_TINY_STRAIN) {
             /* The ratio t / e of the expressions below is 0/0 at e = 0; its limit on the elastic
              * path is E0, so a vanishing effective strain responds elastically, t = E e. */
@@ -122,29 +250,29 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
             return;
         }
         /* Coupling angle, tan(omega) = e_N / sqrt(alpha (e_M^2 + e_L^2)). */
-        double omega = atan2(e[0], sqrt(alpha * eT2));
-        double s = sin(omega), c = cos(omega);
+        S omega = atan2(e[0], sqrt(alpha * eT2));
+        S s = sin(omega), c = cos(omega);
         double r2 = p->r_st * p->r_st;
         /* sigma_0(omega) = sigma_t (-s + sqrt(s^2 + 4 alpha c^2 / r^2)) / (2 alpha c^2 / r^2).
          * Multiplying numerator and denominator by (s + sqrt(s^2 + 4 alpha c^2 / r^2)) gives the
          * same value as 2 sigma_t / (s + sqrt(s^2 + 4 alpha c^2 / r^2)), which stays finite at
          * omega = pi/2 (c = 0); that form is used. */
-        double sigma0 = 2.0 * p->sigma_t / (s + sqrt(s * s + 4.0 * alpha * c * c / r2));
+        S sigma0 = 2.0 * sigma_t / (s + sqrt(s * s + 4.0 * alpha * c * c / r2));
         /* H_0(omega) = H_s/alpha + (H_t - H_s/alpha) (2 omega / pi)^n_t,
          * H_t = 2 E0 / (l_t / l - 1), H_s = r_s E0. */
-        double Ht = 2.0 * E0 / (p->l_t / l - 1.0);
-        double Hs = p->r_s * E0;
-        double H0 = Hs / alpha + (Ht - Hs / alpha) * pow(2.0 * omega / ORC_PI, p->n_t);
-        double e0 = sigma0 / E0;
-        double emax = emax_old > eeff ? emax_old : eeff;
-        double over = emax - e0 > 0.0 ? emax - e0 : 0.0;
-        double sigma_bt = sigma0 * exp(-H0 * over / sigma0);
+        S Ht = 2.0 * E0 / (p->l_t / l - 1.0);
+        S Hs = p->r_s * E0;
+        S H0 = Hs / alpha + (Ht - Hs / alpha) * pow(2.0 * omega / ORC_PI, p->n_t);
+        S e0 = sigma0 / E0;
+        S emax = emax_old > eeff ? emax_old : eeff;
+        S over = emax - e0 > 0.0 ? emax - e0 : 0.0;
+        S sigma_bt = sigma0 * exp(-H0 * over / sigma0);
         /* Incrementally elastic effective traction: t = t_old + E0 (e - e_old), then the vertical
          * return onto 0 <= t <= sigma_bt. */
-        double e_prev[3] = {e[0] - de[0], e[1] - de[1], e[2] - de[2]};
-        double e_old = sqrt(e_prev[0] * e_prev[0] + alpha * (e_prev[1] * e_prev[1] + e_prev[2] * e_prev[2]));
-        double t_eff_old = sqrt(t_old[0] * t_old[0] + (t_old[1] * t_old[1] + t_old[2] * t_old[2]) / alpha);
-        double t = t_eff_old + E0 * (eeff - e_old);
+        S e_prev[3] = {e[0] - de[0], e[1] - de[1], e[2] - de[2]};
+        S e_old = sqrt(e_prev[0] * e_prev[0] + alpha * (e_prev[1] * e_prev[1] + e_prev[2] * e_prev[2]));
+        S t_eff_old = sqrt(t_old[0] * t_old[0] + (t_old[1] * t_old[1] + t_old[2] * t_old[2]) / alpha);
+        S t = t_eff_old + E0 * (eeff - e_old);
         if (t < 0.0) t = 0.0;
         if (t > sigma_bt) t = sigma_bt;
         /* t_N = (t/e) e_N, t_M = alpha (t/e) e_M, t_L = alpha (t/e) e_L */
@@ -155,24 +283,24 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
         return;
     }
     /* App. A.2, compression: t_N incrementally elastic with E_Nc, within -sigma_bc <= t_N <= 0. */
-    double Ed = p->Ed_E0 * E0;
-    double ENc = (-t_old[0] <= p->sigma_c0) ? E0 : Ed;
-    double tN = t_old[0] + ENc * de[0];
-    double eD = e[0] - eV;
-    double eDV = eV + p->beta * eD;
-    double ec0 = p->sigma_c0 / E0;
-    double ec1 = p->kc0 * ec0;
-    double eV0 = p->kc3 * p->sigma_c0 / E0;
-    double rDV = (eV <= 0.0) ? -fabs(eD) / (eV - eV0) : fabs(eD) / eV0;
-    double Hc0 = p->Hc0_E0 * E0, Hc1 = p->Hc1_E0 * E0;
-    double mac = rDV - p->kc1 > 0.0 ? rDV - p->kc1 : 0.0;
-    double Hc = (Hc0 - Hc1) / (1.0 + p->kc2 * mac) + Hc1;
-    double sigma_c1 = p->sigma_c0 + (ec1 - ec0) * Hc;
-    double sigma_bc;
+    S Ed = p->Ed_E0 * E0;
+    S ENc = (-t_old[0] <= p->sigma_c0) ? E0 : Ed;
+    S tN = t_old[0] + ENc * de[0];
+    S eD = e[0] - eV;
+    S eDV = eV + p->beta * eD;
+    S ec0 = p->sigma_c0 / E0;
+    S ec1 = p->kc0 * ec0;
+    S eV0 = p->kc3 * p->sigma_c0 / E0;
+    S rDV = (eV <= 0.0) ? -fabs(eD) / (eV - eV0) : fabs(eD) / eV0;
+    S Hc0 = p->Hc0_E0 * E0, Hc1 = p->Hc1_E0 * E0;
+    S mac = rDV - p->kc1 > 0.0 ? rDV - p->kc1 : 0.0;
+    S Hc = (Hc0 - Hc1) / (1.0 + p->kc2 * mac) + Hc1;
+    S sigma_c1 = p->sigma_c0 + (ec1 - ec0) * Hc;
+    S sigma_bc;
     if (-eDV <= 0.0) {
         sigma_bc = p->sigma_c0;
     } else if (-eDV <= ec1) {
-        double o = -eDV - ec0 > 0.0 ? -eDV - ec0 : 0.0;
+        S o = -eDV - ec0 > 0.0 ? -eDV - ec0 : 0.0;
         sigma_bc = p->sigma_c0 + o * Hc;
     } else {
         sigma_bc = sigma_c1 * exp((-eDV - ec1) * Hc / sigma_c1);
@@ -182,12 +310,12 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
     /* App. A.3, friction: elastic shear trial with stiffness alpha E0, yield surface
      * phi = sqrt(t_M^2 + t_L^2) - sigma_bs(t_N), associated flow.  With the shear stiffness the
      * same in M and L, the return along the normal is a radial scaling onto the circle. */
-    double tM = t_old[1] + alpha * E0 * de[1];
-    double tL = t_old[2] + alpha * E0 * de[2];
-    double sigma_s = p->r_st * p->sigma_t;
+    S tM = t_old[1] + alpha * E0 * de[1];
+    S tL = t_old[2] + alpha * E0 * de[2];
+    S sigma_s = p->r_st * sigma_t;
     double dmu = p->mu0 - p->mu_inf;
-    double sigma_bs = sigma_s + dmu * p->sigma_N0 - p->mu_inf * tN - dmu * p->sigma_N0 * exp(tN / p->sigma_N0);
-    double tau = sqrt(tM * tM + tL * tL);
+    S sigma_bs = sigma_s + dmu * p->sigma_N0 - p->mu_inf * tN - dmu * p->sigma_N0 * exp(tN / p->sigma_N0);
+    S tau = sqrt(tM * tM + tL * tL);
     if (tau > sigma_bs) {
         tM *= sigma_bs / tau;
         tL *= sigma_bs / tau;
@@ -197,51 +325,72 @@ void orc_facet_law(const orc_material *p, double l, const double e[3], const dou
     t_new[2] = tL;
 }
 
+void orc_facet_law(const orc_material *p, double l, const double e[3], const double de[3], double eV,
+                   const double t_old[3], double emax_old, double t_new[3], double *emax_new)
+{
+    facet_law<double>(p, p->E0, p->alpha, p->sigma_t, l, e, de, eV, t_old, emax_old, t_new, emax_new);
+}
+
 /* ------------------------------------------------------------------------------------------ */
 /* Kinematics, Sec. 2, Eq. (1).                                                                 */
 /* ------------------------------------------------------------------------------------------ */
-static void facet_strain(const orc_model *M, const double *q, int32_t k, double e[3])
+template <class S>
+static void facet_strain(const orc_model *M, const S *q, int32_t k, S e[3])
 {
-    const double *uI = q + 6 * (size_t)M->fi[k], *uJ = q + 6 * (size_t)M->fj[k];
-    double rI[3], rJ[3], jump[3];
-    cross3(uI + 3, M->ci + 3 * (size_t)k, rI); /* theta_I x c_I */
-    cross3(uJ + 3, M->cj + 3 * (size_t)k, rJ); /* theta_J x c_J */
-    for (int a = 0; a < 3; ++a) jump[a] = uJ[a] + rJ[a] - uI[a] - rI[a];
+    const S *uI = q + 6 * (size_t)M->fi[k], *uJ = q + 6 * (size_t)M->fj[k];
+    const double *cI = M->ci + 3 * (size_t)k, *cJ = M->cj + 3 * (size_t)k;
+    S jump[3];
+    for (int a = 0; a < 3; ++a) {
+        const int b = (a + 1) % 3, c = (a + 2) % 3;
+        const S rI = uI[3 + b] * cI[c] - uI[3 + c] * cI[b]; /* (theta_I x c_I)_a */
+        const S rJ = uJ[3 + b] * cJ[c] - uJ[3 + c] * cJ[b]; /* (theta_J x c_J)_a */
+        jump[a] = uJ[a] + rJ - uI[a] - rI;
+    }
     double l = M->len[k];
-    e[0] = dot3(M->n + 3 * (size_t)k, jump) / l;
-    e[1] = dot3(M->m + 3 * (size_t)k, jump) / l;
-    e[2] = dot3(M->lv + 3 * (size_t)k, jump) / l;
+    const double *n = M->n + 3 * (size_t)k, *m = M->m + 3 * (size_t)k, *lv = M->lv + 3 * (size_t)k;
+    e[0] = (n[0] * jump[0] + n[1] * jump[1] + n[2] * jump[2]) / l;
+    e[1] = (m[0] * jump[0] + m[1] * jump[1] + m[2] * jump[2]) / l;
+    e[2] = (lv[0] * jump[0] + lv[1] * jump[1] + lv[2] * jump[2]) / l;
 }
 
 /* Linearised volumetric strain of tetrahedron t: (1/3) sum_i gradN_i . u_i  (App. A.2 e_V). */
-static double tet_volumetric_strain(const orc_model *M, const double *q, int32_t t)
+template <class S>
+static S tet_volumetric_strain(const orc_model *M, const S *q, int32_t t)
 {
-    double dv = 0.0;
-    for (int i = 0; i < 4; ++i) dv += dot3(M->gradN + 12 * (size_t)t + 3 * i, q + 6 * (size_t)M->tet[4 * (size_t)t + i]);
+    S dv = 0.0;
+    for (int i = 0; i < 4; ++i) {
+        const double *g = M->gradN + 12 * (size_t)t + 3 * i;
+        const S *u = q + 6 * (size_t)M->tet[4 * (size_t)t + i];
+        dv += g[0] * u[0] + g[1] * u[1] + g[2] * u[2];
+    }
     return dv / 3.0;
 }
 
 /* F_k = A_k P_k t_k; node I receives +F_k and moment c_I x F_k, node J the opposite force and
  * moment -c_J x F_k (Eq. (2a)-(2b) summed over each node's facets). */
-static void facet_force(const orc_model *M, int32_t k, const double t[3], double F[3])
+template <class S>
+static void facet_force(const orc_model *M, int32_t k, const S t[3], S F[3])
 {
     for (int a = 0; a < 3; ++a)
         F[a] = M->area[k] * (M->n[3 * k + a] * t[0] + M->m[3 * k + a] * t[1] + M->lv[3 * k + a] * t[2]);
 }
 
-static void assemble(const orc_model *M, const double *F, double *f_asm)
+template <class S>
+static void assemble(const orc_model *M, const S *F, S *f_asm)
 {
-    memset(f_asm, 0, sizeof(double) * 6 * (size_t)M->N);
+    for (size_t i = 0; i < 6 * (size_t)M->N; ++i) f_asm[i] = 0.0;
     for (int32_t k = 0; k < M->F; ++k) {
-        double mI[3], mJ[3];
-        cross3(M->ci + 3 * (size_t)k, F + 3 * (size_t)k, mI);
-        cross3(M->cj + 3 * (size_t)k, F + 3 * (size_t)k, mJ);
-        double *fI = f_asm + 6 * (size_t)M->fi[k], *fJ = f_asm + 6 * (size_t)M->fj[k];
+        const S *Fk = F + 3 * (size_t)k;
+        const double *cI = M->ci + 3 * (size_t)k, *cJ = M->cj + 3 * (size_t)k;
+        S *fI = f_asm + 6 * (size_t)M->fi[k], *fJ = f_asm + 6 * (size_t)M->fj[k];
         for (int a = 0; a < 3; ++a) {
-            fI[a] += F[3 * k + a];
-            fI[3 + a] += mI[a];
-            fJ[a] -= F[3 * k + a];
-            fJ[3 + a] -= mJ[a];
+            const int b = (a + 1) % 3, c = (a + 2) % 3;
+            const S mI = cI[b] * Fk[c] - cI[c] * Fk[b]; /* (c_I x F)_a */
+            const S mJ = cJ[b] * Fk[c] - cJ[c] * Fk[b]; /* (c_J x F)_a */
+            fI[a] += Fk[a];
+            fI[3 + a] += mI;
+            fJ[a] -= Fk[a];
+            fJ[3 + a] -= mJ;
         }
     }
 }
@@ -261,7 +410,7 @@ void orc_destroy(orc_model *M)
     if (!M) return;
     void *ptrs[] = {M->x, M->tet, M->gradN, M->fi, M->fj, M->ft, M->n, M->m, M->lv, M->ci, M->cj, M->len,
                     M->area, M->mass, M->bc_mask, M->bc_vel, M->f_ext, M->q, M->v, M->f_asm, M->t_loc,
-                    M->emax, M->e_prev, M->F_facet};
+                    M->emax, M->e_prev, M->F_facet, M->pE0, M->palpha, M->psig};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(M);
 }
@@ -431,80 +580,105 @@ orc_model *orc_create(int32_t N, int32_t T, int32_t F, const double *x, const do
  * constrained DOF (zero on free DOFs).  On constrained DOFs g = mass * a with a the acceleration the
  * constraint imposes: 0 when fixed, (vbar(t + dt/2) - vbar(t - dt/2)) / dt when prescribed.  Returns
  * f_ext + R (the part the external world applies). */
-static double ext_force_on_dof(const orc_model *M, size_t i, double t, const double *f_asm)
+template <class S>
+static S ext_force_on_dof(const orc_model *M, size_t i, double t, const S *f_asm)
 {
-    if (M->bc_mask[i] == 0) return M->f_ext[i];
+    if (M->bc_mask[i] == 0) return S(M->f_ext[i]);
     double a = 0.0;
     if (M->bc_mask[i] == 2) a = M->bc_vel[i] * (ramp(M, t + 0.5 * M->dt) - ramp(M, t - 0.5 * M->dt)) / M->dt;
     return M->mass[i] * a - f_asm[i];
 }
 
+/* The evolving part of a trajectory in scalar type S, and the per-facet parameters it runs with
+ * (null: the material's value for every facet). */
+template <class S>
+struct Traj {
+    S *q, *v, *f_asm, *t_loc, *emax, *e_prev, *F;
+    const S *E0, *alpha, *sigma_t;
+};
+
 /* One facet pass at the current q: strains, constitutive update, facet forces, node sums. */
-static void facet_pass(orc_model *M)
+template <class S>
+static void facet_pass(const orc_model *M, Traj<S> &T)
 {
-    double *eV = (double *)malloc(sizeof(double) * ((size_t)M->T + 1));
-    for (int32_t t = 0; t < M->T; ++t) eV[t] = tet_volumetric_strain(M, M->q, t);
+    std::vector<S> eV((size_t)M->T + 1);
+    for (int32_t t = 0; t < M->T; ++t) eV[t] = tet_volumetric_strain(M, T.q, t);
     for (int32_t k = 0; k < M->F; ++k) {
-        double e[3], de[3], tn[3], em;
-        facet_strain(M, M->q, k, e);
-        for (int a = 0; a < 3; ++a) de[a] = e[a] - M->e_prev[3 * k + a];
-        double ev = M->ft[k] >= 0 ? eV[M->ft[k]] : e[0];
-        orc_facet_law(&M->mat, M->len[k], e, de, ev, M->t_loc + 3 * (size_t)k, M->emax[k], tn, &em);
+        S e[3], de[3], tn[3], em;
+        facet_strain(M, T.q, k, e);
+        for (int a = 0; a < 3; ++a) de[a] = e[a] - T.e_prev[3 * k + a];
+        S ev = M->ft[k] >= 0 ? eV[M->ft[k]] : e[0];
+        const S E0 = T.E0 ? T.E0[k] : S(M->mat.E0);
+        const S alpha = T.alpha ? T.alpha[k] : S(M->mat.alpha);
+        const S sigma_t = T.sigma_t ? T.sigma_t[k] : S(M->mat.sigma_t);
+        facet_law<S>(&M->mat, E0, alpha, sigma_t, M->len[k], e, de, ev, T.t_loc + 3 * (size_t)k, T.emax[k], tn, &em);
         for (int a = 0; a < 3; ++a) {
-            M->t_loc[3 * k + a] = tn[a];
-            M->e_prev[3 * k + a] = e[a];
+            T.t_loc[3 * k + a] = tn[a];
+            T.e_prev[3 * k + a] = e[a];
         }
-        M->emax[k] = em;
-        facet_force(M, k, tn, M->F_facet + 3 * (size_t)k);
+        T.emax[k] = em;
+        facet_force(M, k, tn, T.F + 3 * (size_t)k);
     }
-    free(eV);
-    assemble(M, M->F_facet, M->f_asm);
+    assemble(M, T.F, T.f_asm);
 }
 
-int orc_step(orc_model *M, int64_t nsteps)
+/* `nsteps` central-difference steps of trajectory T from step counter *step.  With S = double the
+ * energies are accumulated into W[0] = W_int, W[1] = W_ext (W not null).  With `seed` given, after every step
+ * J += sum over constrained DOFs i of seed_i (f_ext + R)_i. */
+template <class S>
+static void run_steps(const orc_model *M, Traj<S> &T, int64_t nsteps, int64_t *step, double *W, const double *seed,
+                      S *J)
 {
     size_t n6 = 6 * (size_t)M->N;
     double dt = M->dt;
-    double *dq = (double *)malloc(sizeof(double) * n6);
-    double *vh = (double *)malloc(sizeof(double) * n6);
-    double *g_old = (double *)malloc(sizeof(double) * n6);
-    double *fint_old = (double *)malloc(sizeof(double) * n6);
+    std::vector<S> dq(n6), vh(n6), g_old(n6), fint_old(n6);
     for (int64_t s = 0; s < nsteps; ++s) {
-        double t = (double)M->step * dt;
+        double t = (double)*step * dt;
         /* half kick and drift: v_{n+1/2} = v_n + dt/2 a_n ; q_{n+1} = q_n + dt v_{n+1/2} */
         for (size_t i = 0; i < n6; ++i) {
-            g_old[i] = ext_force_on_dof(M, i, t, M->f_asm);
-            fint_old[i] = -M->f_asm[i];
+            g_old[i] = ext_force_on_dof(M, i, t, T.f_asm);
+            fint_old[i] = -T.f_asm[i];
             if (M->bc_mask[i] == 0)
-                vh[i] = M->v[i] + 0.5 * dt * (M->f_ext[i] + M->f_asm[i]) / M->mass[i];
+                vh[i] = T.v[i] + 0.5 * dt * (M->f_ext[i] + T.f_asm[i]) / M->mass[i];
             else if (M->bc_mask[i] == 1)
                 vh[i] = 0.0;
             else
                 vh[i] = M->bc_vel[i] * ramp(M, t + 0.5 * dt);
             dq[i] = dt * vh[i];
-            M->q[i] += dq[i];
+            T.q[i] += dq[i];
         }
         /* internal forces at q_{n+1} */
-        facet_pass(M);
-        M->step += 1;
-        double t1 = (double)M->step * dt;
+        facet_pass(M, T);
+        *step += 1;
+        double t1 = (double)*step * dt;
         /* energies (trapezoid rule on each DOF's increment) and the second half kick */
         for (size_t i = 0; i < n6; ++i) {
-            double g_new = ext_force_on_dof(M, i, t1, M->f_asm);
-            M->W_ext += 0.5 * (g_old[i] + g_new) * dq[i];
-            M->W_int += 0.5 * (fint_old[i] - M->f_asm[i]) * dq[i];
+            S g_new = ext_force_on_dof(M, i, t1, T.f_asm);
+            if constexpr (std::is_same<S, double>::value) {
+                if (W) {
+                    W[1] += 0.5 * (g_old[i] + g_new) * dq[i];
+                    W[0] += 0.5 * (fint_old[i] - T.f_asm[i]) * dq[i];
+                }
+            }
+            if (seed && M->bc_mask[i] != 0) *J += seed[i] * g_new;
             if (M->bc_mask[i] == 0)
-                M->v[i] = vh[i] + 0.5 * dt * (M->f_ext[i] + M->f_asm[i]) / M->mass[i];
+                T.v[i] = vh[i] + 0.5 * dt * (M->f_ext[i] + T.f_asm[i]) / M->mass[i];
             else if (M->bc_mask[i] == 1)
-                M->v[i] = 0.0;
+                T.v[i] = 0.0;
             else
-                M->v[i] = M->bc_vel[i] * ramp(M, t1);
+                T.v[i] = M->bc_vel[i] * ramp(M, t1);
         }
     }
-    free(dq);
-    free(vh);
-    free(g_old);
-    free(fint_old);
+}
+
+int orc_step(orc_model *M, int64_t nsteps)
+{
+    Traj<double> T{M->q, M->v, M->f_asm, M->t_loc, M->emax, M->e_prev, M->F_facet, M->pE0, M->palpha, M->psig};
+    double W[2] = {M->W_int, M->W_ext};
+    run_steps<double>(M, T, nsteps, &M->step, W, NULL, NULL);
+    M->W_int = W[0];
+    M->W_ext = W[1];
+    size_t n6 = 6 * (size_t)M->N;
     for (size_t i = 0; i < n6; ++i)
         if (!isfinite(M->q[i]) || !isfinite(M->v[i])) return -5;
     return 0;
@@ -674,9 +848,10 @@ void orc_facet_march(const orc_material *p, double l, int64_t n, const double *p
  * the paper compares for the uniaxial-strain test).  Both at the current state. */
 void orc_metrics(const orc_model *M, double *w, double *eV)
 {
-    const double E0 = M->mat.E0, aE = M->mat.alpha * M->mat.E0;
     if (w)
         for (int32_t k = 0; k < M->F; ++k) {
+            const double E0 = M->pE0 ? M->pE0[k] : M->mat.E0;
+            const double aE = (M->palpha ? M->palpha[k] : M->mat.alpha) * E0;
             const double *e = M->e_prev + 3 * (size_t)k, *t = M->t_loc + 3 * (size_t)k;
             double wn = e[0] - t[0] / E0;
             if (wn < 0.0) wn = 0.0;
@@ -703,4 +878,111 @@ void orc_set_bc(orc_model *M, const int32_t *mask, const double *vel, double ram
         if (M->bc_mask[i] == 1) M->v[i] = 0.0;
         if (M->bc_mask[i] == 2) M->v[i] = M->bc_vel[i] * ramp(M, t);
     }
+}
+
+/* Per-facet E0, alpha and sigma_t ([F] each, facet order of the model); a null array restores the
+ * material's value for every facet.  The stored tractions are kept: the parameters act from the
+ * next step on. */
+void orc_set_facet_params(orc_model *M, const double *E0, const double *alpha, const double *sigma_t)
+{
+    double **dst[3] = {&M->pE0, &M->palpha, &M->psig};
+    const double *src[3] = {E0, alpha, sigma_t};
+    for (int i = 0; i < 3; ++i) {
+        free(*dst[i]);
+        *dst[i] = NULL;
+        if (src[i]) {
+            *dst[i] = (double *)malloc(sizeof(double) * M->F);
+            memcpy(*dst[i], src[i], sizeof(double) * M->F);
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------------------------ */
+/* Derivatives.                                                                                 */
+/* ------------------------------------------------------------------------------------------ */
+
+/* Jacobian of the constitutive update.  in = (e[3], de[3], eV, t_old[3], e_max_old, E0, alpha,
+ * sigma_t); out = (t_new[3], e_max_new); jac[r * 14 + c] = d out[r] / d in[c].  The other material
+ * parameters are those of *p. */
+void orc_facet_law_jacobian(const orc_material *p, double l, const double in[14], double out[4], double jac[56])
+{
+    typedef Dual<14> S;
+    S x[14];
+    for (int c = 0; c < 14; ++c) {
+        x[c] = S(in[c]);
+        x[c].d[c] = 1.0;
+    }
+    S tn[3], em;
+    facet_law<S>(p, x[11], x[12], x[13], l, x, x + 3, x[6], x + 7, x[10], tn, &em);
+    const S *o[4] = {&tn[0], &tn[1], &tn[2], &em};
+    for (int r = 0; r < 4; ++r) {
+        out[r] = o[r]->v;
+        for (int c = 0; c < 14; ++c) jac[14 * r + c] = o[r]->d[c];
+    }
+}
+
+/* Objective of the adjoint and its directional derivatives.  From the current state, `nsteps` steps
+ * are run (the model itself is left unchanged) and
+ *     J = (1 / nsteps) sum_{n = 1..nsteps} sum_{constrained DOF i} seed_i (f_ext + R)_i (t_n),
+ * the time mean of the seeded reactions.  For each of the nd directions (dE0, dalpha, dsigma_t)[d][F]
+ * of the per-facet parameters, dJ[d] is the derivative of J along it, carried by forward-mode dual
+ * numbers through the same step code (eight directions per pass).  Returns 0, or -5 when the
+ * trajectory became non-finite. */
+/* One trajectory of orc_tangent in scalar type S (double, or a dual number carrying the directions
+ * d0 .. d0 + width - 1). */
+template <class S, int Wd>
+static int tangent_pass(const orc_model *M, int64_t nsteps, const double *seed, int32_t d0, int32_t nd,
+                        const double *dE0, const double *dalpha, const double *dsigma_t, double *J, double *dJ)
+{
+    const size_t n6 = 6 * (size_t)M->N, F = (size_t)M->F;
+    std::vector<S> q(n6), v(n6), f(n6), t(3 * F), em(F), ep(3 * F), Ff(3 * F), E0(F), al(F), sg(F);
+    for (size_t i = 0; i < n6; ++i) {
+        q[i] = S(M->q[i]);
+        v[i] = S(M->v[i]);
+        f[i] = S(M->f_asm[i]);
+    }
+    for (size_t k = 0; k < F; ++k) {
+        for (int a = 0; a < 3; ++a) {
+            t[3 * k + a] = S(M->t_loc[3 * k + a]);
+            ep[3 * k + a] = S(M->e_prev[3 * k + a]);
+        }
+        em[k] = S(M->emax[k]);
+        E0[k] = S(M->pE0 ? M->pE0[k] : M->mat.E0);
+        al[k] = S(M->palpha ? M->palpha[k] : M->mat.alpha);
+        sg[k] = S(M->psig ? M->psig[k] : M->mat.sigma_t);
+        if constexpr (Wd > 0) {
+            for (int w = 0; w < Wd && d0 + w < nd; ++w) {
+                const size_t row = (size_t)(d0 + w) * F + k;
+                if (dE0) E0[k].d[w] = dE0[row];
+                if (dalpha) al[k].d[w] = dalpha[row];
+                if (dsigma_t) sg[k].d[w] = dsigma_t[row];
+            }
+        }
+    }
+    Traj<S> T{q.data(), v.data(), f.data(), t.data(), em.data(), ep.data(), Ff.data(), E0.data(), al.data(), sg.data()};
+    int64_t step = M->step;
+    S Js(0.0);
+    run_steps<S>(M, T, nsteps, &step, NULL, seed, &Js);
+    int rc = 0;
+    for (size_t i = 0; i < n6; ++i)
+        if (!isfinite(value_of(q[i])) || !isfinite(value_of(v[i]))) rc = -5;
+    const double inv = nsteps > 0 ? 1.0 / (double)nsteps : 0.0;
+    if (J) *J = value_of(Js) * inv;
+    if constexpr (Wd > 0) {
+        for (int w = 0; w < Wd && d0 + w < nd; ++w)
+            if (dJ) dJ[d0 + w] = Js.d[w] * inv;
+    }
+    return rc;
+}
+
+int orc_tangent(const orc_model *M, int64_t nsteps, const double *seed, int32_t nd, const double *dE0,
+                const double *dalpha, const double *dsigma_t, double *J, double *dJ)
+{
+    if (nd <= 0) return tangent_pass<double, 0>(M, nsteps, seed, 0, 0, NULL, NULL, NULL, J, NULL);
+    int rc = 0;
+    for (int32_t d0 = 0; d0 < nd; d0 += 8) {
+        int r = tangent_pass<Dual<8>, 8>(M, nsteps, seed, d0, nd, dE0, dalpha, dsigma_t, d0 == 0 ? J : NULL, dJ);
+        if (r) rc = r;
+    }
+    return rc;
 }
