@@ -51,7 +51,7 @@ def gather_pass_bytes(T: int, N: int, r: int) -> float:
 
 def kernel_src_hash() -> str:
     h = hashlib.sha256()
-    for f in ("ldpm_kernels.cu", "ldpm_internal.h"):
+    for f in ("ldpm_kernels.cu", "ldpm_adjoint.cu", "ldpm_device.cuh", "ldpm_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -373,6 +373,147 @@ def run_batch(args, rank, world, local):
     }
 
 
+ADJ_METRIC = "adjoint facet-updates/s (forward, recompute and reverse step per facet) and % of HBM roofline"
+
+
+# Algorithmic bytes of one reverse facet-pass launch (ldpm_adjoint).
+#   per facet        geometry 4r, the step's stored history 4r, carried history adjoint read + written
+#                    8r, gradient accumulators read + written 8r
+#   per tetrahedron  4 particle ids 16 B, its 4 vertex shares written 48r
+#   per particle     the forward record of the step (mixed 84 B, FP64 120 B) and the a_f record
+#                    (mixed 36 B: hi/lo translation, rotation; FP64 48 B)
+def adjoint_facet_bytes(F: int, T: int, N: int, r: int) -> float:
+    return F * 24 * r + T * (16 + 48 * r) + N * ((84 + 36) if r == 4 else (120 + 48))
+
+
+# Algorithmic bytes of one reverse particle-pass launch.
+#   per tetrahedron  4 CSR slot ids and the 4 shares read (48r)
+#   per particle     row pointer 4 B; Qbar, Ubar read and written 192 B; seed 48 B; inverse masses, BC
+#                    codes, specimen 64 B; the a_f record written (mixed 36 B, FP64 48 B)
+def adjoint_gather_bytes(T: int, N: int, r: int) -> float:
+    return T * 4 * (4 + 12 * r) + N * (4 + 192 + 48 + 64 + (36 if r == 4 else 48))
+
+
+def run_adjoint(args, rank, world, local):
+    """Adjoint workload: one ldpm_adjoint of 5000 steps (mixed precision, checkpoints every 250 steps)
+    on the 50 mm tension cube pulled slowly (elastic and pre-peak), gradient of the mean top reaction
+    with respect to every facet's E0, alpha, sigma_t.  Device time by CUDA events on the library's
+    stream around the call; the per-kernel split from a profiled 250-step call; FP64 on 250 steps."""
+    import torch
+
+    from paper_2603_13190_gb300 import ldpm
+
+    torch.cuda.set_device(local)
+    wl, spec, bc = make_inputs("adjoint_uniaxial_tension")
+    N, T, F = spec.n_particles, spec.n_tets, spec.n_facets
+    K, C = wl.steps, 250
+    seed = np.zeros((N, 6))
+    seed[spec.face_nodes(2, 1), 2] = 1.0
+    stream = torch.cuda.Stream()
+    peak, peak_src = measured_peaks()
+    sampler = ClockSampler(local) if rank == 0 else None
+    m = ldpm.Model(spec, wl.material, precision="mixed", bc=bc, stream=stream, device=local)
+    dt = m.dt
+    start = ldpm.ldpm_save_checkpoint(m.h)
+    for _ in range(args.warmup):
+        ldpm.ldpm_load_checkpoint(m.h, start)
+        m.adjoint(C, seed, C)
+    ldpm.ldpm_load_checkpoint(m.h, start)
+    if sampler:
+        sampler.__enter__()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+    t0 = time.perf_counter()
+    J, gE, ga, gs = m.adjoint(K, seed, C)
+    wall = time.perf_counter() - t0
+    with torch.cuda.stream(stream):
+        e1.record(stream)
+    stream.synchronize()
+    dev_ms = barrier_max(world, e0.elapsed_time(e1))
+    wall = barrier_max(world, wall)
+    if sampler:
+        sampler.__exit__()
+    # kernel split: a profiled call of C steps from the same start
+    ldpm.ldpm_load_checkpoint(m.h, start)
+    ldpm.ldpm_profile(m.h, True)
+    m.adjoint(C, seed, C)
+    kms, kcnt = ldpm.ldpm_profile_read(m.h)
+    ldpm.ldpm_profile(m.h, False)
+    m.close()
+    rf_ms, rg_ms = kms[3] / max(1, kcnt[3]), kms[4] / max(1, kcnt[4])
+    fb, gb = adjoint_facet_bytes(F, T, N, 4), adjoint_gather_bytes(T, N, 4)
+    achieved = fb / (rf_ms * 1e-3) / 1e9
+    # FP64 on C steps
+    m64 = ldpm.Model(spec, wl.material, precision="fp64", dt=dt, bc=bc, stream=stream, device=local)
+    m64.adjoint(16, seed, 16)
+    ldpm.ldpm_profile(m64.h, True)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        a0.record(stream)
+    m64.adjoint(C, seed, C)
+    with torch.cuda.stream(stream):
+        a1.record(stream)
+    stream.synchronize()
+    k64, c64 = ldpm.ldpm_profile_read(m64.h)
+    m64.close()
+    fp64_value = F * C / (a0.elapsed_time(a1) * 1e-3)
+    rf64 = k64[3] / max(1, c64[3])
+    fb64 = adjoint_facet_bytes(F, T, N, 8)
+    value = world * F * K / (dev_ms * 1e-3)
+    return {
+        "metric": ADJ_METRIC, "value": value, "unit": "facet-updates/s", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "adjoint_uniaxial_tension", "cube_mm": wl.edge, "particles": N, "tets": T,
+                   "facets": F, "steps": K, "checkpoint_every": C, "dt_s": dt,
+                   "objective": "time mean of the top-face u_z reaction", "parameters": "E0, alpha, sigma_t per facet",
+                   "precision": "mixed: FP32 facet terms, FP64 particle adjoints and gradient totals",
+                   "l2": "working set (step inputs of a 250-step segment, 7.9 GB) far above L2; no flush",
+                   "warmup": "%d adjoint calls of %d steps" % (args.warmup, C)},
+        "objective_J": J, "grad_abs_max": [float(np.abs(x).max()) for x in (gE, ga, gs)],
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": recorded_traffic("adjoint_facet_kernel", "adjoint_uniaxial_tension", "mixed"),
+                     "algorithmic_bytes_per_launch": fb, "peak_source": peak_src, "kernel": "adjoint_facet_kernel"},
+        "gather_roofline": {"achieved": gb / (rg_ms * 1e-3) / 1e9, "frac": gb / (rg_ms * 1e-3) / 1e9 / peak,
+                            "algorithmic_bytes_per_launch": gb},
+        "kernel_ms": {"facet": kms[1] / max(1, kcnt[1]), "gather": kms[2] / max(1, kcnt[2]),
+                      "reverse_facet": rf_ms, "reverse_gather": rg_ms},
+        "fp64": {"value": fp64_value, "steps": C, "reverse_facet_ms": rf64,
+                 "reverse_facet_frac": fb64 / (rf64 * 1e-3) / 1e9 / peak},
+        "e2e": {"value": world * F * K / wall, "unit": "facet-updates/s", "h2d_bytes_per_step": seed.nbytes / K,
+                "d2h_bytes_per_step": (3 * F * 8 + 8) / K, "seconds": wall,
+                "what": "one ldpm_adjoint call: seed from host memory, gradients to host memory"},
+        "gpu_launches": 2 * K + 2 * K + K + 2 * (K // C + 1),
+        "clocks": sampler.summary() if sampler else None,
+    }
+
+
+def cpu_baseline_adjoint(spec, wl, bc, dt, budget_s: float = 20.0):
+    """The oracle's derivative path as it stands: forward-mode dual numbers carrying 8 parameter
+    directions through its FP64 step, single thread, a bounded number of full steps."""
+    import oracle
+
+    o = oracle.Oracle(spec, wl.material, dt, bc)
+    seed = np.zeros((spec.n_particles, 6))
+    seed[spec.face_nodes(2, 1), 2] = 1.0
+    rng = np.random.default_rng(0)
+    d = rng.standard_normal((8, spec.n_facets))
+    n, el = 1, 0.0
+    while True:
+        t0 = time.perf_counter()
+        o.tangent(n, seed, dE0=d)
+        el = time.perf_counter() - t0
+        if el > budget_s / 3 or n >= 8:
+            break
+        n *= 2
+    return {"value": spec.n_facets * n / el, "unit": "facet-updates/s", "cores": 1, "kind": "oracle",
+            "sample": "%d steps of the full %d-facet specimen carrying 8 directional derivatives (forward mode, "
+                      "%.1f s, single thread); the oracle has no reverse mode" % (n, spec.n_facets, el)}
+
+
 def cpu_baseline(spec, wl, bc, dt, budget_s: float = 20.0):
     """The FP64 oracle as it stands, single thread on the host, on a bounded sample of the workload."""
     import oracle
@@ -430,7 +571,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--workload", default="uniaxial_tension",
                     choices=("uniaxial_tension", "confined_compression", "elastic_vibration",
-                             "batched_unconfined_compression"))
+                             "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", choices=("mixed", "fp64"), default=None,
@@ -457,6 +598,22 @@ def main():
             print(json.dumps(res), flush=True)
         return
     rank, world, local = dist_setup(args.gpus)
+    if args.workload == "adjoint_uniaxial_tension":
+        res = run_adjoint(args, rank, world, local)
+        if rank == 0:
+            if world == 1 and not args.no_cpu_baseline:
+                from paper_2603_13190_gb300 import workloads
+
+                wl = workloads.WORKLOADS["adjoint_uniaxial_tension"]
+                spec = wl.specimen()
+                res["cpu_baseline"] = cpu_baseline_adjoint(spec, wl, workloads.workload_bc(wl.name, spec),
+                                                           res["config"]["dt_s"])
+            print(json.dumps(res), flush=True)
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.destroy_process_group()
+        return
     if args.workload == "batched_unconfined_compression":
         res = run_batch(args, rank, world, local)
         if rank == 0:

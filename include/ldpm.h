@@ -180,7 +180,8 @@ int ldpm_info(ldpm_t h, int64_t info[5], double *dt);
 
 /* Per-kernel CUDA-event timing of ldpm_step on the handle's stream.  enable = 1 starts (and
  * clears) recording, 0 stops.  ldpm_profile_read fills ms[k] (summed milliseconds) and count[k]
- * (launches) for k = 0 kick, 1 facet pass, 2 gather+update; n = entries the caller provides. */
+ * (launches) for k = 0 kick, 1 facet pass, 2 gather+update, 3 reverse facet pass and 4 reverse
+ * particle pass (ldpm_adjoint); n = entries the caller provides (at most 5 are written). */
 int ldpm_profile(ldpm_t h, int32_t enable);
 int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n);
 
@@ -231,6 +232,46 @@ int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt);
  * particle pass (set by defaults, the LDPM_TETS_PER_BLOCK / LDPM_GATHER_LANES environment variables
  * at create, or the autotuner).  Library service; no counterpart in the paper. */
 int ldpm_launch_shape(ldpm_t h, int32_t shape[2]);
+
+/* ---- Per-facet parameters and the adjoint.  The paper uses one material for all facets and has no
+ * derivatives; these serve sensitivity and calibration studies of its explicit step (Sec. 3,
+ * App. A).  Single-specimen handles only (LDPM_E_INVALID_ARG for batches). */
+
+/* Give facet k its own E0[k], alpha[k], sigma_t[k] (caller facet order, [F] each, finite and > 0)
+ * in place of the material's; a NULL array keeps the material's value for that parameter, all three
+ * NULL restore the material everywhere.  The constants derived from them (App. A: sigma_s = r_st
+ * sigma_t, H_c0 = (H_c0/E0) E0, e_c0 = sigma_c0 / E0, ...) follow per facet.  Acts from the next step;
+ * the stored tractions are kept and dt is not re-estimated.  Synchronises the stream.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+int ldpm_set_facet_params(ldpm_t h, const double *E0, const double *alpha, const double *sigma_t);
+
+/* Run `nsteps` steps from the current state (as ldpm_step would; the handle ends in the same state)
+ * and return the objective
+ *     J = (1 / nsteps) sum_{n=1..nsteps} sum_{constrained DOF i} seed[i] R_i(t_n),
+ * the time mean of the seeded reactions R = m a - f of the fixed and prescribed DOFs (seed [6*N],
+ * caller particle order, entries of free DOFs ignored; e.g. 1 on the u_z DOFs of the loaded face
+ * gives its mean reaction force), with its gradient with respect to every facet's E0, alpha and
+ * sigma_t (gE0, galpha, gsigma_t: [F] each in caller facet order; any may be NULL).  The reverse
+ * pass needs the states of the forward run in reverse order: the state is checkpointed on the device
+ * every `ckpt_every` steps, and each segment is recomputed once, keeping its steps' inputs.  Device
+ * memory: (nsteps / ckpt_every + 1) states plus ckpt_every step inputs (mixed mode: 96 B per particle
+ * and 16 B per facet each).  Arithmetic in the model's precision (mixed: FP32 facet terms, FP64
+ * particle adjoints and gradient totals).  Derivatives at points where the law is not differentiable
+ * (a switch of branch, sqrt at 0) are those of the branch the forward value takes.  With gE0, galpha
+ * and gsigma_t all NULL only the forward run and J are computed.  Synchronous.
+ * Errors: INVALID_ARG, OOM (checkpoint memory), UNSTABLE (non-finite state or gradient), CUDA. */
+int ldpm_adjoint(ldpm_t h, int64_t nsteps, int32_t ckpt_every, const double *seed, double *J, double *gE0,
+                 double *galpha, double *gsigma_t);
+
+/* The constitutive update (App. A) and its vector-Jacobian product on the device, for n independent
+ * facet states (a test and analysis hook; no counterpart in the paper).  in [n][16] = l, e_N, e_M,
+ * e_L, de_N, de_M, de_L, e_V, t_N, t_M, t_L (previous tractions), e_max (previous), E0, alpha,
+ * sigma_t, 0 (the remaining parameters from *mat).  adj_out [n][4] = adjoints of the new t_N, t_M,
+ * t_L, e_max.  Writes out [n][4] = new t_N, t_M, t_L, e_max and adj_in [n][16] = the adjoints of the
+ * inputs in the layout of `in` (slots 0 and 15 zero).  precision: LDPM_FP64 or LDPM_MIXED (FP32
+ * law).  Synchronous; uses the current CUDA device.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+int ldpm_facet_law_vjp(int32_t precision, const ldpm_material *mat, int64_t n, const double *in, const double *adj_out,
+                       double *out, double *adj_in);
 
 /* Release everything the handle owns (synchronises first).  NULL is a no-op. */
 void ldpm_destroy(ldpm_t h);

@@ -1,4 +1,4 @@
-"""Build libldpm.so in-tree with nvcc for sm_103a (two translation units compiled in parallel)."""
+"""Build libldpm.so in-tree with nvcc for sm_103a (translation units compiled in parallel)."""
 from __future__ import annotations
 
 import concurrent.futures as cf
@@ -11,7 +11,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libldpm.so")
-SOURCES = ("ldpm_kernels.cu", "ldpm_api.cu", "ldpm_noalloc.cu")
+SOURCES = ("ldpm_kernels.cu", "ldpm_api.cu", "ldpm_noalloc.cu", "ldpm_adjoint.cu")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -42,7 +42,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     def compile_one(src):
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         extra = []
-        if src == "ldpm_kernels.cu":
+        if src in ("ldpm_kernels.cu", "ldpm_adjoint.cu"):
             # approximate FP32 division and square root: only the mixed-mode arithmetic is FP32
             extra = ["-prec-div=false", "-prec-sqrt=false"]
         cmd = [nvcc()] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]

@@ -115,6 +115,13 @@ void law_const(const ldpm_material &mt, double dt, LawConst<R> &c)
     // FP32: squares of strains below ~1e-19 underflow; 1e-15 keeps every product of the law normal
     // and changes tractions by < E0 * 1e-15.  FP64: the oracle's threshold.
     c.tiny_strain = R(sizeof(R) == 4 ? 1e-15 : 1e-150);
+    c.four_over_r2 = R(4.0 / (mt.r_st * mt.r_st));
+    c.r_st = R(mt.r_st);
+    c.Hc0_E0 = R(mt.Hc0_E0);
+    c.Hc1_E0 = R(mt.Hc1_E0);
+    c.kc0 = R(mt.kc0);
+    c.kc3 = R(mt.kc3);
+    c.Ed_E0 = R(mt.Ed_E0);
     c.elastic = mt.elastic;
 }
 
@@ -149,8 +156,8 @@ struct ldpm_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::pair<int, int>> ev_pairs;  // (kernel id, event index of start)
-    double prof_ms[3] = {0, 0, 0};
-    int64_t prof_cnt[3] = {0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};  // kick, facet pass, particle pass, reverse facet, reverse particle
+    int64_t prof_cnt[5] = {0, 0, 0, 0, 0};
     size_t rsize() const { return prec == LDPM_MIXED ? sizeof(float) : sizeof(double); }
     size_t r4size() const { return 4 * rsize(); }
 };
@@ -165,7 +172,7 @@ void free_model(ldpm_ctx *h)
                     h->dm.tet,
                     h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
-                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16};
+                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_out16) cudaFreeHost(h->h_out16);
@@ -891,6 +898,24 @@ int collect_profile(ldpm_ctx *h)
     return LDPM_OK;
 }
 
+// Run `launch`; while profiling, bracket it with events on the stream (kernel id kid).
+template <class Fn>
+int timed(ldpm_ctx *h, int kid, Fn &&launch)
+{
+    if (!h->prof) return launch();
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+        return fail(LDPM_E_CUDA, "event create failed");
+    h->ev_pool.push_back(a);
+    h->ev_pool.push_back(b);
+    h->ev_pairs.push_back({kid, (int)h->ev_pool.size() - 2});
+    CU(cudaEventRecord(a, h->stream));
+    int rc = launch();
+    if (rc) return rc;
+    CU(cudaEventRecord(b, h->stream));
+    return LDPM_OK;
+}
+
 int check_flag(ldpm_ctx *h)
 {
     int32_t fl = 0;
@@ -935,6 +960,183 @@ int download_state(ldpm_ctx *h, std::vector<double> &ps, std::vector<double> *hi
             return fail(LDPM_E_CUDA, "history download: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
     CU(cudaStreamSynchronize(h->stream));
+    return LDPM_OK;
+}
+
+// ---- per-facet parameters and the adjoint -------------------------------------------------------
+
+// Device allocations released together.
+struct DevArena {
+    std::vector<void *> ptrs;
+    ~DevArena()
+    {
+        for (void *p : ptrs) cudaFree(p);
+    }
+    template <class T>
+    int get(T **p, size_t count)
+    {
+        int rc = dalloc(p, count);
+        if (rc == LDPM_OK) ptrs.push_back(*p);
+        return rc;
+    }
+};
+
+// Byte sizes of the evolving state: everything a step reads and writes.
+struct StateBytes {
+    size_t ps, pd, pm, hist;
+    size_t total() const { return ps + pd + pm + hist + 256; }
+};
+
+StateBytes state_bytes(const ldpm_ctx *h)
+{
+    StateBytes b;
+    b.ps = 16 * (size_t)h->dm.N * sizeof(double);
+    b.pd = 8 * (size_t)h->dm.N * sizeof(double);
+    b.pm = h->dm.pm32 ? (size_t)kMirror * h->dm.N * sizeof(float) : 0;
+    b.hist = 12 * (size_t)h->dm.T * h->r4size();
+    return b;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Copy the evolving state to (save) or from (restore) a slot of `total()` bytes.
+int state_copy(ldpm_ctx *h, char *slot, bool save)
+{
+    const StateBytes b = state_bytes(h);
+    struct {
+        void *dev;
+        size_t n;
+    } parts[] = {{h->dm.pstate, b.ps}, {h->dm.pdyn, b.pd}, {h->dm.pm32, b.pm}, {h->dm.hist, b.hist}, {h->dm.step, 8}};
+    size_t off = 0;
+    for (auto &pt : parts) {
+        if (pt.n) {
+            if (save)
+                CU(cudaMemcpyAsync(slot + off, pt.dev, pt.n, cudaMemcpyDeviceToDevice, h->stream));
+            else
+                CU(cudaMemcpyAsync(pt.dev, slot + off, pt.n, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        off += align256(pt.n);
+    }
+    return LDPM_OK;
+}
+
+size_t slot_stride(const ldpm_ctx *h)
+{
+    const StateBytes b = state_bytes(h);
+    return align256(b.ps) + align256(b.pd) + align256(b.pm) + align256(b.hist) + 256;
+}
+
+template <class R>
+int adjoint_run(ldpm_ctx *h, int64_t K, int64_t C, const double *seed, double *J, double *gE0, double *galpha,
+                double *gsigma)
+{
+    const SpecHost &S = h->sp[0];
+    const int64_t N = h->dm.N, Fint = 12 * (int64_t)h->dm.T;
+    const bool mixed = sizeof(R) == 4;
+    int rc;
+    // c = -seed / K on constrained DOFs (internal order)
+    std::vector<double> c(6 * (size_t)N, 0.0);
+    for (int32_t i = 0; i < S.N; ++i) {
+        const size_t P = (size_t)S.p0 + S.inv_p[i];
+        uint64_t bc;
+        std::memcpy(&bc, &h->pconst_h[8 * P + 6], 8);
+        for (int d = 0; d < 6; ++d)
+            if ((bc >> (8 * d)) & 0xffu) c[6 * P + d] = -seed[6 * (size_t)i + d] / (double)K;
+    }
+    const int64_t nseg = (K + C - 1) / C;
+    const size_t stride = slot_stride(h);
+    const size_t rec = mixed ? (size_t)kMirror * N * sizeof(float) : 16 * (size_t)N * sizeof(double);
+    const size_t hb = (size_t)Fint * sizeof(R4<R>);
+    const size_t snap_stride = align256(rec) + align256(hb);
+    DevArena ar;
+    char *ckpt = nullptr, *snap = nullptr;
+    AdjointModel a;
+    if ((rc = ar.get(&ckpt, stride * (size_t)(nseg + 1))) || (rc = ar.get(&snap, snap_stride * (size_t)std::min(C, K))))
+        return fail(LDPM_E_OOM, "adjoint: %lld checkpoints of %zu bytes and %lld step snapshots of %zu bytes do "
+                                "not fit (use a smaller checkpoint interval)",
+                    (long long)(nseg + 1), stride, (long long)std::min(C, K), snap_stride);
+    if ((rc = ar.get((double **)&a.cseed, 6 * (size_t)N)) || (rc = ar.get(&a.Qbar, 6 * (size_t)N)) ||
+        (rc = ar.get(&a.Ubar, 6 * (size_t)N)) || (rc = ar.get(&a.jacc, (size_t)N)) ||
+        (rc = ar.get((R4<R> **)&a.adj_h, (size_t)Fint)) || (rc = ar.get((R4<R> **)&a.gacc, (size_t)Fint)) ||
+        (rc = ar.get((R **)&a.tvc2, 4 * (size_t)Fint)))
+        return rc;
+    if (mixed) {
+        if ((rc = ar.get((float **)&a.af, 12 * (size_t)N)) || (rc = ar.get(&a.gsum, 4 * (size_t)Fint))) return rc;
+    } else {
+        if ((rc = ar.get((double **)&a.af, 8 * (size_t)N))) return rc;
+    }
+    CU(cudaMemcpyAsync(a.cseed, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CU(cudaMemsetAsync(a.jacc, 0, (size_t)N * sizeof(double), h->stream));
+    auto fwd = [&](bool objective) -> int {
+        int r;
+        if ((r = timed(h, 1, [&]() { return launch_facet_any(h, FACET_STEP, nullptr); })) ||
+            (r = timed(h, 2, [&]() { return launch_gather_any(h, GATHER_STEP_MID, nullptr); })))
+            return r;
+        if (objective) CU(launch_objective(h->dm, a, h->stream));
+        return LDPM_OK;
+    };
+    // forward sweep: checkpoint at the start of every segment, and the final state
+    for (int64_t sg = 0; sg < nseg; ++sg) {
+        if ((rc = state_copy(h, ckpt + stride * sg, true))) return rc;
+        const int64_t n = std::min(C, K - sg * C);
+        for (int64_t i = 0; i < n; ++i)
+            if ((rc = fwd(true))) return rc;
+    }
+    if ((rc = state_copy(h, ckpt + stride * nseg, true))) return rc;
+    if ((rc = check_flag(h))) return rc;
+    const bool grads = gE0 || galpha || gsigma;
+    // reverse sweep
+    if (grads) {
+    CU(launch_adjoint_init<R>(h->dm, a, h->stream));
+    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+        if ((rc = state_copy(h, ckpt + stride * sg, false))) return rc;
+        const int64_t n = std::min(C, K - sg * C);
+        for (int64_t i = 0; i < n; ++i) {  // recompute, keeping each step's inputs
+            char *sl = snap + snap_stride * i;
+            CU(cudaMemcpyAsync(sl, mixed ? (const void *)h->dm.pm32 : (const void *)h->dm.pstate, rec,
+                               cudaMemcpyDeviceToDevice, h->stream));
+            CU(cudaMemcpyAsync(sl + align256(rec), h->dm.hist, hb, cudaMemcpyDeviceToDevice, h->stream));
+            if ((rc = fwd(false))) return rc;
+        }
+        for (int64_t i = n - 1; i >= 0; --i) {
+            char *sl = snap + snap_stride * i;
+            a.snap_p = sl;
+            a.snap_h = sl + align256(rec);
+            if ((rc = timed(h, 3, [&]() -> int {
+                     CU(launch_adjoint_facet<R>(h->dm, a, h->stream));
+                     return LDPM_OK;
+                 })) ||
+                (rc = timed(h, 4, [&]() -> int {
+                     CU(launch_adjoint_gather<R>(h->dm, a, h->stream));
+                     return LDPM_OK;
+                 })))
+                return rc;
+        }
+        if (mixed) CU(launch_adjoint_fold<R>(h->dm, a, h->stream));
+    }
+    if ((rc = state_copy(h, ckpt + stride * nseg, false))) return rc;
+    }
+    // results
+    std::vector<double> jp((size_t)N);
+    CU(cudaMemcpyAsync(jp.data(), a.jacc, jp.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    std::vector<double> g4(grads ? 4 * (size_t)Fint : 0);
+    if (grads)
+        CU(cudaMemcpyAsync(g4.data(), mixed ? (const void *)a.gsum : (const void *)a.gacc, g4.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    if (J) {
+        double acc = 0.0;
+        for (double x : jp) acc += x;
+        *J = acc;
+    }
+    double *outs[3] = {gE0, galpha, gsigma};
+    for (int k3 = 0; k3 < 3; ++k3)
+        if (outs[k3])
+            for (int32_t k = 0; k < S.F; ++k) outs[k3][k] = g4[4 * (size_t)S.fmap[k] + k3];
+    for (int k3 = 0; k3 < 3; ++k3)
+        if (outs[k3])
+            for (int32_t k = 0; k < S.F; ++k)
+                if (!std::isfinite(outs[k3][k])) return fail(LDPM_E_UNSTABLE, "adjoint: non-finite gradient");
     return LDPM_OK;
 }
 
@@ -1300,7 +1502,7 @@ int ldpm_profile(ldpm_t h, int32_t enable)
     DevGuard dg(h->device);
     if (h->prof) collect_profile(h);
     h->prof = enable != 0;
-    for (int k = 0; k < 3; ++k) {
+    for (int k = 0; k < 5; ++k) {
         h->prof_ms[k] = 0;
         h->prof_cnt[k] = 0;
     }
@@ -1314,7 +1516,7 @@ int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n)
     DevGuard dg(h->device);
     int rc = collect_profile(h);
     if (rc) return rc;
-    for (int k = 0; k < n && k < 3; ++k) {
+    for (int k = 0; k < n && k < 5; ++k) {
         if (ms) ms[k] = h->prof_ms[k];
         if (count) count[k] = h->prof_cnt[k];
     }
@@ -1439,6 +1641,114 @@ int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt)
     }
     if (dt) *dt = S.dt;
     return LDPM_OK;
+}
+
+int ldpm_set_facet_params(ldpm_t h, const double *E0, const double *alpha, const double *sigma_t)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "per-facet parameters take a single-specimen model");
+    DevGuard dg(h->device);
+    try {
+        const SpecHost &S = h->sp[0];
+        const int64_t Fint = 12 * (int64_t)h->dm.T;
+        const double *src[3] = {E0, alpha, sigma_t};
+        const double mat[3] = {S.mat.E0, S.mat.alpha, S.mat.sigma_t};
+        for (int k3 = 0; k3 < 3; ++k3)
+            if (src[k3])
+                for (int32_t k = 0; k < S.F; ++k)
+                    if (!(std::isfinite(src[k3][k]) && src[k3][k] > 0.0))
+                        return fail(LDPM_E_INVALID_ARG, "per-facet parameter %d of facet %d is not finite and > 0", k3, k);
+        CU(cudaStreamSynchronize(h->stream));
+        for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);  // captured launches hold the old model
+        h->graphs.clear();
+        if (!E0 && !alpha && !sigma_t) {
+            if (h->dm.pf) cudaFree(h->dm.pf);
+            h->dm.pf = nullptr;
+            return LDPM_OK;
+        }
+        std::vector<double> v(4 * (size_t)Fint, 0.0);
+        for (int64_t f = 0; f < Fint; ++f)
+            for (int k3 = 0; k3 < 3; ++k3) v[4 * f + k3] = mat[k3];
+        for (int k3 = 0; k3 < 3; ++k3)
+            if (src[k3])
+                for (int32_t k = 0; k < S.F; ++k) v[4 * (size_t)S.fmap[k] + k3] = src[k3][k];
+        if (!h->dm.pf) {
+            int rc = h->prec == LDPM_MIXED ? dalloc((float4 **)&h->dm.pf, (size_t)Fint)
+                                           : dalloc((double4a **)&h->dm.pf, (size_t)Fint);
+            if (rc) return rc;
+        }
+        if (h->prec == LDPM_MIXED) {
+            std::vector<float> f32(v.begin(), v.end());
+            CU(cudaMemcpy(h->dm.pf, f32.data(), f32.size() * sizeof(float), cudaMemcpyHostToDevice));
+        } else {
+            CU(cudaMemcpy(h->dm.pf, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice));
+        }
+        return LDPM_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
+int ldpm_adjoint(ldpm_t h, int64_t nsteps, int32_t ckpt_every, const double *seed, double *J, double *gE0,
+                 double *galpha, double *gsigma_t)
+{
+    g_err.clear();
+    if (!h || nsteps < 1 || ckpt_every < 1 || !seed)
+        return fail(LDPM_E_INVALID_ARG, "bad handle, nsteps < 1, ckpt_every < 1 or NULL seed");
+    if (h->sp.size() != 1) return fail(LDPM_E_INVALID_ARG, "the adjoint takes a single-specimen model");
+    DevGuard dg(h->device);
+    try {
+        CU(cudaStreamSynchronize(h->stream));
+        return h->prec == LDPM_MIXED ? adjoint_run<float>(h, nsteps, ckpt_every, seed, J, gE0, galpha, gsigma_t)
+                                     : adjoint_run<double>(h, nsteps, ckpt_every, seed, J, gE0, galpha, gsigma_t);
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    } catch (...) {
+        return fail(LDPM_E_CUDA, "unexpected exception in ldpm_adjoint");
+    }
+}
+
+int ldpm_facet_law_vjp(int32_t precision, const ldpm_material *mat, int64_t n, const double *in, const double *adj_out,
+                       double *out, double *adj_in)
+{
+    g_err.clear();
+    if (!mat || n < 0 || (n > 0 && (!in || !adj_out || !out || !adj_in)) ||
+        (precision != LDPM_FP64 && precision != LDPM_MIXED))
+        return fail(LDPM_E_INVALID_ARG, "bad precision, material, count or NULL buffer");
+    int rc = check_material(*mat);
+    if (rc) return rc;
+    if (n == 0) return LDPM_OK;
+    try {
+        DevArena ar;
+        double *d_in, *d_ao, *d_out, *d_ai;
+        if ((rc = ar.get(&d_in, 16 * (size_t)n)) || (rc = ar.get(&d_ao, 4 * (size_t)n)) ||
+            (rc = ar.get(&d_out, 4 * (size_t)n)) || (rc = ar.get(&d_ai, 16 * (size_t)n)))
+            return rc;
+        CU(cudaMemcpy(d_in, in, 16 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(d_ao, adj_out, 4 * (size_t)n * sizeof(double), cudaMemcpyHostToDevice));
+        cudaError_t e;
+        if (precision == LDPM_MIXED) {
+            LawConst<float> c, *dc;
+            law_const<float>(*mat, 0.0, c);
+            if ((rc = ar.get(&dc, 1))) return rc;
+            CU(cudaMemcpy(dc, &c, sizeof(c), cudaMemcpyHostToDevice));
+            e = launch_law_vjp<float>(dc, n, d_in, d_ao, d_out, d_ai, 0);
+        } else {
+            LawConst<double> c, *dc;
+            law_const<double>(*mat, 0.0, c);
+            if ((rc = ar.get(&dc, 1))) return rc;
+            CU(cudaMemcpy(dc, &c, sizeof(c), cudaMemcpyHostToDevice));
+            e = launch_law_vjp<double>(dc, n, d_in, d_ao, d_out, d_ai, 0);
+        }
+        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "law VJP launch: %s", cudaGetErrorString(e));
+        CU(cudaDeviceSynchronize());
+        CU(cudaMemcpy(out, d_out, 4 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+        CU(cudaMemcpy(adj_in, d_ai, 16 * (size_t)n * sizeof(double), cudaMemcpyDeviceToHost));
+        return LDPM_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
 }
 
 int ldpm_launch_shape(ldpm_t h, int32_t shape[2])

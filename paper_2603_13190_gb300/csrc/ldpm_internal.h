@@ -13,6 +13,7 @@
 //   tet    [T]     int4 particle ids of the 4 vertices (-1: padding tetrahedron)
 //   geo    [12T]   R4   c_a (arm from the edge's first vertex to the facet centroid), projected area A
 //   hist   [12T]   R4   t_N, t_M, t_L, e_max
+//   pf     [12T]   R4   optional per-facet E0, alpha, sigma_t, 0 (null: the material's values)
 //   fout   [12T]   R4   facet force acting on the edge's first vertex, 0 (written only when forces
 //                       are rebuilt from history, for ldpm_facet_forces)
 //   tvc    [T][4][6] R  per tetrahedron vertex: sum of its 6 facets' force (3) and moment about the
@@ -55,6 +56,9 @@ struct LawConst {
     R mu_diff_sN0, mu_inf, inv_sigma_N0, sigma_s;
     R dt;
     R tiny_strain;  // fracture branch: effective strains below this respond elastically
+    // ratios from which the constants above that depend on E0, alpha, sigma_t are rebuilt per facet
+    // (facet_params): 4 / r_st^2, r_st, H_c0/E0, H_c1/E0, kappa_c0, kappa_c3, E_d/E0
+    R four_over_r2, r_st, Hc0_E0, Hc1_E0, kc0, kc3, Ed_E0;
     int32_t elastic;
 };
 
@@ -82,12 +86,34 @@ struct DeviceModel {
     double *bc_vm = nullptr;        // [N][6] prescribed velocity times the DOF's mass
     int4 *tet = nullptr;
     void *geo = nullptr, *hist = nullptr, *fout = nullptr, *tvc = nullptr, *ent = nullptr;
+    void *pf = nullptr;             // per-facet E0, alpha, sigma_t (R4 [12T]) or null
     int32_t *row = nullptr;
     int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)
     void *law = nullptr;            // LawConst<R>[n_spec]
     SpecDyn *spec = nullptr;        // [n_spec]
     int64_t *step = nullptr;        // step counter (one for all specimens)
     int32_t *flag = nullptr;        // non-finite state seen
+};
+
+// Reverse (adjoint) pass workspace (ldpm_adjoint.cu).  The objective is
+//   J = sum_n sum_i c_i f_i(t_n),  c = -seed / K on constrained DOFs, 0 elsewhere
+// (the time mean of the seeded reactions R = m a - f), and its gradient with respect to the
+// per-facet E0, alpha, sigma_t.  Reverse step n reads the inputs of forward step n: the particle
+// records it read (snap_p: pm32 layout in mixed mode, pstate layout in FP64) and the history before it
+// (snap_h).
+//   af     [N][8] f64 (FP64) or [N][12] f32 (mixed: a_u hi(3) lo(3), a_theta(3), pad(3)):
+//          a_f = c + dt M^-1 Ubar, the adjoint of the node forces of the step being reversed
+//   adj_h  [12T] R4  adjoint of the history (t_N, t_M, t_L, e_max) of the step before it
+//   gacc   [12T] R4  gradient accumulators (E0, alpha, sigma_t, 0)
+//   tvc2   [T][4][12] R  per tetrahedron vertex: sums of the facets' displacement adjoints (6) and
+//          velocity adjoints (6)
+//   Qbar, Ubar [N][6] f64  adjoints of q_n and v_{n-1/2}
+struct AdjointModel {
+    const void *snap_p = nullptr, *snap_h = nullptr;
+    void *af = nullptr, *adj_h = nullptr, *gacc = nullptr, *tvc2 = nullptr;
+    double *Qbar = nullptr, *Ubar = nullptr, *cseed = nullptr;
+    double *gsum = nullptr;  // [12T][4] FP64 totals (mixed mode: gacc is folded here per segment)
+    double *jacc = nullptr;  // [N] per-particle shares of the objective, summed over the forward steps
 };
 
 // Message returned by ldpm_last_error() on the calling thread (ldpm_api.cu).
@@ -112,6 +138,29 @@ cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *
                           cudaStream_t s);
 template <class R>
 cudaError_t launch_hist_to_user(const DeviceModel &m, double *out5, cudaStream_t s);
+
+// Adjoint launchers (ldpm_adjoint.cu).
+// Reset: af = c, Qbar = Ubar = 0, adj_h = 0, gacc = 0 (and gsum = 0).
+template <class R>
+cudaError_t launch_adjoint_init(const DeviceModel &m, const AdjointModel &a, cudaStream_t s);
+// Reverse of one step: the facet pass (law VJP, parameter gradients, per-vertex sums), then the
+// particle pass (Qbar, Ubar and the next a_f).
+template <class R>
+cudaError_t launch_adjoint_facet(const DeviceModel &m, const AdjointModel &a, cudaStream_t s);
+template <class R>
+cudaError_t launch_adjoint_gather(const DeviceModel &m, const AdjointModel &a, cudaStream_t s);
+// gsum += gacc, gacc = 0 (mixed mode, at the end of each reversed segment).
+template <class R>
+cudaError_t launch_adjoint_fold(const DeviceModel &m, const AdjointModel &a, cudaStream_t s);
+// After a forward step (node forces f_n in pdyn, step counter n): jacc[p] += sum_d seed_pd R_pd(t_n) / K
+// with seed / K = -c, i.e. the particle's share of the objective.
+cudaError_t launch_objective(const DeviceModel &m, const AdjointModel &a, cudaStream_t s);
+// Device evaluation of the facet law and its vector-Jacobian product on independent inputs:
+// in [n][16] = l, e(3), de(3), eV, t_old(3), e_max_old, E0, alpha, sigma_t, 0; adj_out [n][4];
+// out [n][4] = t_new(3), e_max_new; adj_in [n][16] (same layout as in, slot 0 = 0).
+template <class R>
+cudaError_t launch_law_vjp(const LawConst<R> *law, int64_t n, const double *in, const double *adj_out, double *out,
+                           double *adj_in, cudaStream_t s);
 template <class R>
 cudaError_t launch_hist_from_user(const DeviceModel &m, const double *in5, cudaStream_t s);
 

@@ -17,158 +17,11 @@
 
 #include <cuda_runtime.h>
 
+#include "ldpm_device.cuh"
 #include "ldpm_internal.h"
 
 namespace ldpm {
 namespace {
-
-constexpr double kPi = 3.14159265358979323846;
-
-// ------------------------------------------------------------------------------------------------
-// Small vector helpers.
-// ------------------------------------------------------------------------------------------------
-template <class R>
-struct V3 {
-    R x, y, z;
-};
-template <class R>
-__device__ __forceinline__ V3<R> operator-(V3<R> a, V3<R> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-template <class R>
-__device__ __forceinline__ V3<R> operator+(V3<R> a, V3<R> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-template <class R>
-__device__ __forceinline__ V3<R> operator*(R s, V3<R> a) { return {s * a.x, s * a.y, s * a.z}; }
-template <class R>
-__device__ __forceinline__ R dot(V3<R> a, V3<R> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-template <class R>
-__device__ __forceinline__ V3<R> cross(V3<R> a, V3<R> b)
-{
-    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-
-__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double rsqrt_(double x) { return 1.0 / sqrt(x); }
-
-// Exponentials of the facet law.  FP64 mode: the library functions.  Mixed mode: the hardware
-// approximations (exp via ex2, x^y via lg2/ex2; errors of a few ulp, far inside the mixed-mode
-// tolerances).  This translation unit is compiled with approximate FP32 division and square root
-// (-prec-div=false -prec-sqrt=false), which touches only the mixed-mode arithmetic.
-__device__ __forceinline__ float exp_(float x) { return __expf(x); }
-__device__ __forceinline__ double exp_(double x) { return exp(x); }
-// x^y for x >= 0, y >= 0
-__device__ __forceinline__ float powpos_(float x, float y)
-{
-    return x > 0.0f ? exp2f(y * __log2f(x)) : (y == 0.0f ? 1.0f : 0.0f);
-}
-__device__ __forceinline__ double powpos_(double x, double y) { return pow(x, y); }
-
-// Tangent pair (m, l) of a unit normal n: the branch-free orthonormal basis of Duff et al.,
-// "Building an Orthonormal Basis, Revisited" (JCGT 6(1), 2017).  Any orthonormal tangents are
-// allowed (paper Sec. 2); this choice is continuous except across n_z = 0.
-template <class R>
-__device__ __forceinline__ void tangent_frame(V3<R> n, V3<R> &m, V3<R> &l)
-{
-    const R sgn = copysign(R(1), n.z);
-    const R a = R(-1) / (sgn + n.z);
-    const R b = n.x * n.y * a;
-    m = {R(1) + sgn * n.x * n.x * a, sgn * b, -sgn * n.x};
-    l = {b, sgn + n.y * n.y * a, -n.y};
-}
-
-// ------------------------------------------------------------------------------------------------
-// Appendix A constitutive update of one facet.  e: strain, de: its increment over this step, eV:
-// volumetric strain of the tetrahedron, l: facet (edge) length; t/emax: previous history in,
-// new history out.
-// ------------------------------------------------------------------------------------------------
-template <class R>
-__device__ __forceinline__ void facet_law(const LawConst<R> &c, R l, V3<R> e, V3<R> de, R eV, R &tN, R &tM,
-                                          R &tL, R &emax)
-{
-    const R E0 = c.E0, alpha = c.alpha;
-    if (c.elastic) {  // Sec. 2: t = E0 diag(1, alpha, alpha) e
-        tN = E0 * e.x;
-        tM = alpha * E0 * e.y;
-        tL = alpha * E0 * e.z;
-        return;
-    }
-    if (e.x > R(0)) {
-        // App. A.1 fracture.  Effective strain, coupling angle omega (sin = e_N / e,
-        // cos = sqrt(alpha e_T^2) / e), strength sigma_0(omega) written as
-        // 2 sigma_t / (sin + sqrt(sin^2 + 4 alpha cos^2 / r_st^2)) (the paper's expression with
-        // numerator and denominator multiplied by the conjugate; finite at omega = pi/2).
-        const R aT2 = alpha * (e.y * e.y + e.z * e.z);
-        const R eeff = sqrt(e.x * e.x + aT2);
-        if (eeff < c.tiny_strain) {
-            // t / e is 0/0 at vanishing strain (its squares underflow first); the elastic limit
-            // t = E e applies.  Reached ahead of a loading wave, where strains decay to ~0.
-            tN = E0 * e.x;
-            tM = alpha * E0 * e.y;
-            tL = alpha * E0 * e.z;
-            emax = emax > eeff ? emax : eeff;
-            return;
-        }
-        const R saT = sqrt(aT2);
-        const R omega = atan2(e.x, saT);
-        const R inv_e = R(1) / eeff;
-        const R sn = e.x * inv_e, cs = saT * inv_e;
-        const R sigma0 = R(2) * c.sigma_t / (sn + sqrt(sn * sn + c.four_alpha_over_r2 * cs * cs));
-        // H_t = 2 E0 / (l_t / l - 1) = 2 E0 l / (l_t - l); H_0 = H_s/alpha + (H_t - H_s/alpha)(2 omega/pi)^n_t
-        const R Ht = R(2) * E0 * l / (c.l_t - l);
-        const R H0 = c.Hs_over_alpha + (Ht - c.Hs_over_alpha) * powpos_(omega * R(2.0 / kPi), c.n_t);
-        const R e0 = sigma0 / E0;
-        emax = emax > eeff ? emax : eeff;
-        const R over = emax - e0 > R(0) ? emax - e0 : R(0);
-        const R sigma_bt = sigma0 * exp_(-H0 * over / sigma0);
-        // t = t_old + E0 (e - e_old).  The effective-strain difference is formed from the increment:
-        // e^2 - e_old^2 = sum_i w_i de_i (2 e_i - de_i) with w = (1, alpha, alpha), divided by
-        // (e + e_old) -- algebraically the same, free of the cancellation of two nearby roots.
-        const V3<R> ep = e - de;
-        const R e_old = sqrt(ep.x * ep.x + alpha * (ep.y * ep.y + ep.z * ep.z));
-        const R num = de.x * (e.x + ep.x) + alpha * (de.y * (e.y + ep.y) + de.z * (e.z + ep.z));
-        const R d_eff = num / (eeff + e_old);
-        const R t_old = sqrt(tN * tN + (tM * tM + tL * tL) * c.inv_alpha);
-        R t = t_old + E0 * d_eff;
-        t = t < R(0) ? R(0) : t;
-        t = t > sigma_bt ? sigma_bt : t;
-        const R r = t * inv_e;
-        tN = r * e.x;
-        tM = alpha * r * e.y;
-        tL = alpha * r * e.z;
-        return;
-    }
-    // App. A.2 compression: t_N incrementally elastic (E_Nc), -sigma_bc <= t_N <= 0.
-    const R ENc = (-tN <= c.sigma_c0) ? E0 : c.Ed;
-    R tn = tN + ENc * de.x;
-    const R eD = e.x - eV;
-    const R eDV = eV + c.beta * eD;
-    const R rDV = (eV <= R(0)) ? -fabs(eD) / (eV - c.eV0) : fabs(eD) / c.eV0;
-    const R mac = rDV - c.kc1 > R(0) ? rDV - c.kc1 : R(0);
-    const R Hc = (c.Hc0 - c.Hc1) / (R(1) + c.kc2 * mac) + c.Hc1;
-    R sigma_bc;
-    if (-eDV <= R(0)) {
-        sigma_bc = c.sigma_c0;
-    } else if (-eDV <= c.ec1) {
-        const R o = -eDV - c.ec0 > R(0) ? -eDV - c.ec0 : R(0);
-        sigma_bc = c.sigma_c0 + o * Hc;
-    } else {
-        const R sigma_c1 = c.sigma_c0 + (c.ec1 - c.ec0) * Hc;
-        sigma_bc = sigma_c1 * exp_((-eDV - c.ec1) * Hc / sigma_c1);
-    }
-    tn = tn < -sigma_bc ? -sigma_bc : tn;
-    tn = tn > R(0) ? R(0) : tn;
-    // App. A.3 friction: elastic shear trial, radial return onto sqrt(t_M^2 + t_L^2) = sigma_bs(t_N).
-    R tm = tM + alpha * E0 * de.y;
-    R tl = tL + alpha * E0 * de.z;
-    const R sigma_bs = c.sigma_s + c.mu_diff_sN0 - c.mu_inf * tn - c.mu_diff_sN0 * exp_(tn * c.inv_sigma_N0);
-    const R tau2 = tm * tm + tl * tl;
-    if (tau2 > sigma_bs * sigma_bs) {
-        const R s = sigma_bs * rsqrt_(tau2);
-        tm *= s;
-        tl *= s;
-    }
-    tN = tn;
-    tM = tm;
-    tL = tl;
-}
 
 // ------------------------------------------------------------------------------------------------
 // Facet pass.  A block owns TETS consecutive tetrahedra (12 * TETS facets, one thread each).
@@ -195,36 +48,8 @@ struct Stride {
     static constexpr int con = sizeof(R) == 4 ? 12 : 14;
 };
 
-template <class R>
-struct VecT;
-template <>
-struct VecT<float> {
-    using v16 = float4;  // 16-byte vector
-    using v2 = float2;   // pair
-    static __device__ __forceinline__ void put(float *d, const float *s) { *reinterpret_cast<float4 *>(d) = float4{s[0], s[1], s[2], s[3]}; }
-    static __device__ __forceinline__ void get(float *d, const float *s)
-    {
-        const float4 w = *reinterpret_cast<const float4 *>(s);
-        d[0] = w.x;
-        d[1] = w.y;
-        d[2] = w.z;
-        d[3] = w.w;
-    }
-};
-template <>
-struct VecT<double> {
-    using v16 = double2;
-    using v2 = double2;
-    static __device__ __forceinline__ void put(double *d, const double *s) { *reinterpret_cast<double2 *>(d) = double2{s[0], s[1]}; }
-    static __device__ __forceinline__ void get(double *d, const double *s)
-    {
-        const double2 w = *reinterpret_cast<const double2 *>(s);
-        d[0] = w.x;
-        d[1] = w.y;
-    }
-};
-
-template <class R, int MODE, int TETS>
+// PF: the facet's own E0, alpha, sigma_t (m.pf) replace the material's in the law.
+template <class R, int MODE, int TETS, bool PF>
 __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const void *__restrict__ vsrc)
 {
     using T4 = R4<R>;
@@ -249,10 +74,11 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
     const int slot = tid - 12 * j;
     const int64_t f = tet0 * 12 + tid;
     const bool valid = tet0 + j < m.T;
-    T4 g{}, h{};
+    T4 g{}, h{}, pp{};
     if (valid) {
         g = geo[f];
         if (MODE != FACET_ELASTIC) h = hist[f];
+        if (PF) pp = static_cast<const T4 *>(m.pf)[f];
     }
 
     // ---- phase A: vertex records -> shared memory, e_V per tetrahedron
@@ -387,7 +213,9 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
         const V3<R> cb = ca - d;
         R tN, tM, tL, emax;
         const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;  // specimens are padded to 32 tetrahedra
-        const LawConst<R> &c = lawc[sp];
+        LawConst<R> cpf;
+        if constexpr (PF) cpf = facet_params(lawc[sp], pp.x, pp.y, pp.z);
+        const LawConst<R> &c = PF ? cpf : lawc[sp];
         if (MODE == FACET_FROM_HIST) {
             tN = h.x;
             tM = h.y;
@@ -498,99 +326,6 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 // per ~64 cycles per sub-partition, so FP64 instruction count, not bytes, bounds this pass if the
 // whole warp serves one particle.
 // ------------------------------------------------------------------------------------------------
-// ramp(t) = clamp(t / T, 0, 1), given invT = 1/T (invT = 0: no ramp, ramp = 1)
-__device__ __forceinline__ double ramp(double t, double invT)
-{
-    if (invT == 0.0) return 1.0;
-    const double r = t * invT;
-    return r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
-}
-
-
-// Finite test on the exponent bits (integer pipe).
-__device__ __forceinline__ bool finite_bits(double x)
-{
-    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
-}
-
-// IEEE-754 conversions done with integer instructions.  The GB300 FP64 pipe (which also executes
-// F2F conversions) issues one warp instruction per ~64 cycles per sub-partition; these bit
-// manipulations run at integer rate.  Magnitudes below the normal float range become signed zeros
-// (|x| < 1.2e-38 in mm, N or rad: never significant for the facet pass).
-__device__ __forceinline__ float d2f_trunc(double x)  // mantissa truncated: error < 1 float ulp
-{
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int eb = (int)((b >> 52) & 0x7ff);
-    const int e = eb - 1023 + 127;
-    if (e <= 0) return __uint_as_float(sign);
-    if (e >= 255) {  // overflow -> inf; NaN stays NaN
-        const bool nan = eb == 0x7ff && (b & 0xfffffffffffffull) != 0;
-        return __uint_as_float(sign | 0x7f800000u | (nan ? 0x400000u : 0u));
-    }
-    return __uint_as_float(sign | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
-}
-
-// x = hi + lo: hi the truncated float of x, lo the truncated float of the 29 dropped mantissa bits
-// (relative error of hi + lo below 2^-46).
-__device__ __forceinline__ void d2f_split(double x, float &hi, float &lo)
-{
-    const uint64_t b = (uint64_t)__double_as_longlong(x);
-    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
-    const int eb = (int)((b >> 52) & 0x7ff);
-    const int e = eb - 1023 + 127;
-    if (e <= 0 || e >= 255) {
-        hi = d2f_trunc(x);
-        lo = 0.0f;
-        return;
-    }
-    hi = __uint_as_float(sign | ((uint32_t)e << 23) | (uint32_t)((b >> 29) & 0x7fffffu));
-    const uint32_t rem = (uint32_t)(b & 0x1fffffffu);  // value rem * 2^(eb - 1075)
-    const int lz = __clz(rem);                         // 32 when rem == 0
-    const int fe = (31 - lz) + eb - 1075 + 127;        // float exponent of the remainder
-    if (rem == 0 || fe <= 0) {
-        lo = 0.0f;
-        return;
-    }
-    const uint32_t frac = ((uint32_t)((uint64_t)rem << (lz + 1))) >> 9;  // leading one dropped
-    lo = __uint_as_float(sign | ((uint32_t)fe << 23) | frac);
-}
-
-// float -> double (exact for normal floats; float denormals become signed zeros).
-__device__ __forceinline__ double f2d_bits(float f)
-{
-    const uint32_t u = __float_as_uint(f);
-    const uint64_t sign = (uint64_t)(u & 0x80000000u) << 32;
-    const uint32_t e = (u >> 23) & 0xffu;
-    if (e == 0) return __longlong_as_double((long long)sign);
-    const uint64_t ed = e == 255 ? 0x7ffull : (uint64_t)(e + 896);
-    return __longlong_as_double((long long)(sign | (ed << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
-}
-
-// FP32 mirror entries of DOF d of a particle after its FP64 q and v changed.
-__device__ __forceinline__ void write_mirror(float *pm, int d, double q, double v)
-{
-    if (d < 3) {
-        float hi, lo;
-        d2f_split(q, hi, lo);
-        pm[6 + d] = hi;
-        pm[9 + d] = lo;
-        pm[15 + d] = d2f_trunc(v);
-    } else {
-        pm[12 + d - 3] = d2f_trunc(q);
-        pm[18 + d - 3] = d2f_trunc(v);
-    }
-}
-
-template <class R>
-__device__ __forceinline__ double to_double(R x)
-{
-    if constexpr (sizeof(R) == 4)
-        return f2d_bits(x);
-    else
-        return x;
-}
-
 template <class R, int MODE, int LPP>
 __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
@@ -934,24 +669,33 @@ __global__ void hist_from_user_kernel(DeviceModel m, const double *__restrict__ 
     static_cast<R4<R> *>(m.hist)[f] = h;
 }
 
-template <class R, int MODE>
-cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t s)
+template <class R, int MODE, bool PF>
+cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t s)
 {
     const int tpb = m.tets_per_block;
     const unsigned blocks = (unsigned)((m.T + tpb - 1) / tpb);
     if (blocks == 0) return cudaSuccess;
     switch (tpb) {
     case 16:
-        facet_kernel<R, MODE, 16><<<blocks, 192, 0, s>>>(m, pst);
+        facet_kernel<R, MODE, 16, PF><<<blocks, 192, 0, s>>>(m, pst);
         break;
     case 32:
-        facet_kernel<R, MODE, 32><<<blocks, 384, 0, s>>>(m, pst);
+        facet_kernel<R, MODE, 32, PF><<<blocks, 384, 0, s>>>(m, pst);
         break;
     default:
-        facet_kernel<R, MODE, 8><<<blocks, 96, 0, s>>>(m, pst);
+        facet_kernel<R, MODE, 8, PF><<<blocks, 96, 0, s>>>(m, pst);
         break;
     }
     return cudaGetLastError();
+}
+
+// Per-facet parameters matter only where the law or E0 / alpha enter: the step and the metrics.
+template <class R, int MODE>
+cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t s)
+{
+    if constexpr (MODE == FACET_STEP || MODE == FACET_METRIC)
+        if (m.pf) return launch_facet_pf<R, MODE, true>(m, pst, s);
+    return launch_facet_pf<R, MODE, false>(m, pst, s);
 }
 
 }  // namespace

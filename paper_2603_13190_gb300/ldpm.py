@@ -95,6 +95,9 @@ def lib():
             "ldpm_batch_metrics": ([P, I32, P, P], C.c_int),
             "ldpm_batch_info": ([P, I32, P, P], C.c_int),
             "ldpm_launch_shape": ([P, P], C.c_int),
+            "ldpm_set_facet_params": ([P, P, P, P], C.c_int),
+            "ldpm_adjoint": ([P, I64, I32, P, P, P, P, P], C.c_int),
+            "ldpm_facet_law_vjp": ([I32, P, I64, P, P, P, P], C.c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
@@ -295,9 +298,11 @@ def ldpm_profile(h, enable: bool) -> None:
 
 
 def ldpm_profile_read(h):
-    ms = np.zeros(3)
-    cnt = np.zeros(3, np.int64)
-    _check(lib().ldpm_profile_read(h, _ptr(ms), _ptr(cnt), 3), "ldpm_profile_read")
+    """Summed milliseconds and launch counts: kick, facet pass, particle pass, reverse facet pass,
+    reverse particle pass."""
+    ms = np.zeros(5)
+    cnt = np.zeros(5, np.int64)
+    _check(lib().ldpm_profile_read(h, _ptr(ms), _ptr(cnt), 5), "ldpm_profile_read")
     return ms, cnt
 
 
@@ -329,6 +334,41 @@ def ldpm_kinetic_energy_noalloc(v_dev: int, mass_dev: int, n_dof: int, out_dev: 
     _check(lib().ldpm_kinetic_energy_noalloc(C.c_void_p(v_dev), C.c_void_p(mass_dev), int(n_dof),
                                              C.c_void_p(out_dev), _stream_handle(stream)),
            "ldpm_kinetic_energy_noalloc")
+
+
+def ldpm_set_facet_params(h, F: int, E0=None, alpha=None, sigma_t=None) -> None:
+    """Per-facet E0 / alpha / sigma_t ([F] each, facet order; None = the material's value)."""
+    arrs = [None if a is None else np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (F,)))
+            for a in (E0, alpha, sigma_t)]
+    _check(lib().ldpm_set_facet_params(h, *[_ptr(a) for a in arrs]), "ldpm_set_facet_params")
+
+
+def ldpm_adjoint(h, N: int, F: int, nsteps: int, seed, ckpt_every: int = 250, grads: bool = True):
+    """Objective J (time mean of the seeded reactions over the next nsteps steps; seed [N, 6]) and its
+    gradient with respect to per-facet E0, alpha, sigma_t ([F] each).  Advances the model by nsteps."""
+    seed = np.ascontiguousarray(seed, np.float64).reshape(N, 6)
+    J = C.c_double(0.0)
+    g = [np.zeros(F) for _ in range(3)] if grads else [None, None, None]
+    _check(lib().ldpm_adjoint(h, int(nsteps), int(ckpt_every), _ptr(seed), C.byref(J), *[_ptr(x) for x in g]),
+           "ldpm_adjoint")
+    return J.value, g[0], g[1], g[2]
+
+
+def ldpm_facet_law_vjp(precision: int, material: dict, inp, adj_out):
+    """Device law and its vector-Jacobian product on independent rows (layouts in include/ldpm.h):
+    inp [n, 16], adj_out [n, 4] -> (out [n, 4], adj_in [n, 16])."""
+    inp = np.ascontiguousarray(inp, np.float64).reshape(-1, 16)
+    adj_out = np.ascontiguousarray(adj_out, np.float64).reshape(-1, 4)
+    n = inp.shape[0]
+    out = np.zeros((n, 4))
+    adj_in = np.zeros((n, 16))
+    m = Material()
+    for f in MATERIAL_FIELDS:
+        setattr(m, f, float(material[f]))
+    m.elastic = int(material.get("elastic", 0))
+    _check(lib().ldpm_facet_law_vjp(int(precision), C.byref(m), n, _ptr(inp), _ptr(adj_out), _ptr(out), _ptr(adj_in)),
+           "ldpm_facet_law_vjp")
+    return out, adj_in
 
 
 def ldpm_last_error() -> str:
@@ -424,3 +464,10 @@ class Model:
 
     def info(self):
         return ldpm_info(self.h)
+
+    def set_facet_params(self, E0=None, alpha=None, sigma_t=None):
+        ldpm_set_facet_params(self.h, self.F, E0, alpha, sigma_t)
+
+    def adjoint(self, nsteps: int, seed, ckpt_every: int = 250, grads: bool = True):
+        """(J, dJ/dE0, dJ/dalpha, dJ/dsigma_t); the model advances by nsteps."""
+        return ldpm_adjoint(self.h, self.N, self.F, nsteps, seed, ckpt_every, grads)

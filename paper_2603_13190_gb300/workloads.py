@@ -11,7 +11,10 @@ seeded synthetic cube that stands in for one of the paper's benchmark families (
                           test, Sec. 4.2), 100 mm cube, ~12.5M facets, mixed precision;
   * batched_unconfined_compression -- 64 random cubes of edge U(30, 60) mm, d = 2..4 mm, unconfined
                           compression between frictionless ("free") platens (Sec. 4.5), stepped as one
-                          batch; particle counts scale with volume from uniaxial_tension's density.
+                          batch; particle counts scale with volume from uniaxial_tension's density;
+  * adjoint_uniaxial_tension -- the uniaxial_tension cube pulled slowly (top u_z at 5 mm/s): 5000 steps
+                          stay elastic and before the peak; gradient of the mean top reaction with
+                          respect to every facet's E0, alpha, sigma_t (the paper has no derivatives).
 
 Boundary-condition codes per degree of freedom (u_x, u_y, u_z, theta_x, theta_y, theta_z):
   0 = free, 1 = fixed (velocity 0), 2 = prescribed velocity bc_vel * ramp(t),
@@ -141,6 +144,11 @@ def confined_compression_bc(spec: Specimen, velocity: float = 25.0, phase: int =
     return bc
 
 
+def adjoint_tension_bc(spec: Specimen, velocity: float = 5.0, ramp_time: float = 4e-4) -> BoundaryConditions:
+    """uniaxial_tension_bc at a slow rate: 5000 steps end at about 60 % of the peak load."""
+    return uniaxial_tension_bc(spec, velocity=velocity, ramp_time=ramp_time)
+
+
 def unconfined_compression_bc(spec: Specimen, velocity: float = 50.0, ramp_time: float = 2e-4) -> BoundaryConditions:
     """Unconfined compression with free platens as in Sec. 4.5: on the top and bottom faces u_z is
     prescribed (top moving down at `velocity`, bottom held) and theta_x, theta_y are fixed, while u_x,
@@ -194,6 +202,8 @@ WORKLOADS = {
                                  200000),
     "confined_compression": Workload("confined_compression", 100.0, 3.0, 6.0, 165000, 1,
                                      dict(WORKLOAD_MATERIAL), "mixed", 50000),
+    "adjoint_uniaxial_tension": Workload("adjoint_uniaxial_tension", 50.0, 2.0, 4.0, 25000, 1,
+                                         dict(WORKLOAD_MATERIAL), "mixed", 5000),
 }
 # (the batched workload is built by batch_specimens / batch_recipe; material WORKLOAD_MATERIAL with
 # the friction of the workload definition: mu_0 = 0.2, mu_inf = 0, sigma_N0 = 600 MPa)
@@ -208,4 +218,6 @@ def workload_bc(name: str, spec: Specimen) -> BoundaryConditions:
         return confined_compression_bc(spec)
     if name == "batched_unconfined_compression":
         return unconfined_compression_bc(spec)
+    if name == "adjoint_uniaxial_tension":
+        return adjoint_tension_bc(spec)
     raise KeyError(name)

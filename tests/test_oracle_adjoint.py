@@ -16,48 +16,13 @@ import numpy as np
 import pytest
 
 import oracle
+from law_cases import CASES, IN_SCALE, L_FACET, law_point
 from paper_2603_13190_gb300 import specimen, workloads
 from paper_2603_13190_gb300.specimen import Specimen
 from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
 
 MAT = dict(WORKLOAD_MATERIAL)
-L_FACET = 3.0
-SCALE = np.array([1e-4] * 3 + [1e-6] * 3 + [1e-4] + [1.0] * 3 + [1e-4] + [MAT["E0"], MAT["alpha"], MAT["sigma_t"]])
-
-
-def _lin(a, b, n):
-    return np.linspace(a, b, n)
-
-
-def _law_point(path, eV, i, mat=MAT):
-    """Inputs of the law at step i of a strain path driven from zero (state from the steps before)."""
-    t, em = oracle.facet_march(mat, L_FACET, path, eV)
-    return np.concatenate([path[i], path[i] - path[i - 1], [eV[i]], t[i - 1], [em[i - 1]],
-                           [mat["E0"], mat["alpha"], mat["sigma_t"]]])
-
-
-def _cases():
-    n = 40
-    z = np.zeros(n)
-    c = {}
-    c["fracture_elastic"] = (np.stack([_lin(0, 4e-5, n), _lin(0, 1e-5, n), _lin(0, -4e-6, n)], 1), z, 30)
-    c["fracture_softening"] = (np.stack([_lin(0, 3e-4, n), _lin(0, 4e-5, n), _lin(0, 1e-5, n)], 1), z, 35)
-    up = np.stack([_lin(0, 3e-4, n), _lin(0, 4e-5, n), _lin(0, 1e-5, n)], 1)
-    down = np.stack([_lin(3e-4, 2.9e-4, n), _lin(4e-5, 3.9e-5, n), _lin(1e-5, 1e-5, n)], 1)
-    c["fracture_unloading"] = (np.vstack([up, down]), np.zeros(2 * n), n + 10)
-    c["compression_elastic"] = (np.stack([_lin(0, -2e-4, n), _lin(0, 3e-5, n), _lin(0, -2e-5, n)], 1),
-                                _lin(0, -1e-4, n), 30)
-    c["friction_return"] = (np.stack([_lin(0, -1e-4, n), _lin(0, 1.6e-3, n), _lin(0, 8e-4, n)], 1),
-                            _lin(0, -5e-5, n), 35)
-    c["hardening_linear"] = (np.stack([_lin(0, -8e-3, n), _lin(0, 1e-4, n), z], 1), _lin(0, -5.5e-3, n), 35)
-    c["hardening_exponential"] = (np.stack([_lin(0, -2e-2, n), _lin(0, 1e-4, n), z], 1), _lin(0, -1.2e-2, n), 35)
-    comp = np.stack([_lin(0, -8e-3, n), _lin(0, 1e-4, n), z], 1)
-    back = np.array([[-2e-3, 1e-4, 0.0], [-1.9e-3, 1e-4, 0.0]])
-    c["normal_clamped_at_zero"] = (np.vstack([comp, back]), np.concatenate([_lin(0, -5.5e-3, n), [-3e-3, -3e-3]]), n)
-    return c
-
-
-CASES = _cases()
+SCALE = IN_SCALE
 
 
 def _sigma_bs(tN, mat=MAT):
@@ -69,7 +34,7 @@ def _sigma_bs(tN, mat=MAT):
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_law_jacobian_matches_central_differences(name):
     path, eV, i = CASES[name]
-    x = _law_point(path, eV, i)
+    x = law_point(path, eV, i)
     out, jac = oracle.facet_law_jacobian(MAT, L_FACET, x)
     # the point lies in the intended branch
     e, t_old, em_old = x[0:3], x[7:10], x[10]
