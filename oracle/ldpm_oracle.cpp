@@ -30,7 +30,11 @@
  *   - e_V of a tetrahedron is its linearised volumetric strain Delta V / (3 V0) = (1/3) div u;
  *   - in the fracture branch an effective strain below 1e-150 (where t/e is 0/0 in floating point)
  *     takes the elastic limit t = E e;
- *   - k_t > 0 (tensile reloading), E_d != E0 and r_s != 0 are outside what is pinned here.
+ *   - k_t > 0: on reloading from zero effective traction, only the part of the effective-strain
+ *     increment above e_tr = k_t (e_max - sigma_bt / E0) counts (k_t = 0: the clamp alone);
+ *   - r_s != 0 enters H_0 through H_s = r_s E0; the paper gives no law for the cohesion
+ *     degradation it mentions, so sigma_s stays constant;
+ *   - E_Nc = E_d when -t_N,old > sigma_c0, as written.
  *
  * Derivatives (the paper has none; they serve the adjoint of the explicit step).  The law and the
  * step are templates over the scalar type.  Instantiated with `double` they are the reference step;
@@ -272,7 +276,15 @@ static void facet_law(const orc_material *p, S E0, S alpha, S sigma_t, double l,
         S e_prev[3] = {e[0] - de[0], e[1] - de[1], e[2] - de[2]};
         S e_old = sqrt(e_prev[0] * e_prev[0] + alpha * (e_prev[1] * e_prev[1] + e_prev[2] * e_prev[2]));
         S t_eff_old = sqrt(t_old[0] * t_old[0] + (t_old[1] * t_old[1] + t_old[2] * t_old[2]) / alpha);
-        S t = t_eff_old + E0 * (eeff - e_old);
+        S de_eff = eeff - e_old;
+        if (p->k_t > 0.0 && t_eff_old <= 0.0 && de_eff > 0.0) {
+            /* Reloading from zero traction: the traction stays zero until the effective strain
+             * reaches e_tr = k_t (e_max - sigma_bt / E0), then grows elastically (App. A.1).  With
+             * k_t = 0, e_tr = 0 and the whole increment counts (the clamp alone). */
+            S e_tr = p->k_t * (emax - sigma_bt / E0);
+            if (e_tr > e_old) de_eff = eeff > e_tr ? eeff - e_tr : S(0.0);
+        }
+        S t = t_eff_old + E0 * de_eff;
         if (t < 0.0) t = 0.0;
         if (t > sigma_bt) t = sigma_bt;
         /* t_N = (t/e) e_N, t_M = alpha (t/e) e_M, t_L = alpha (t/e) e_L */

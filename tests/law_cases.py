@@ -41,7 +41,33 @@ def cases():
     comp = np.stack([lin(0, -8e-3, n), lin(0, 1e-4, n), z], 1)
     back = np.array([[-2e-3, 1e-4, 0.0], [-1.9e-3, 1e-4, 0.0]])
     c["normal_clamped_at_zero"] = (np.vstack([comp, back]), np.concatenate([lin(0, -5.5e-3, n), [-3e-3, -3e-3]]), n)
+    # the unload/reload variants (the material overrides are the fourth entry)
+    e0 = MAT["sigma_t"] / MAT["E0"]
+    soft = np.stack([lin(0, 3 * e0, n), lin(0, 0.3 * e0, n), lin(0, 0.1 * e0, n)], 1)
+    unl = np.stack([lin(3 * e0, 0.2 * e0, n), lin(0.3 * e0, 0.02 * e0, n), lin(0.1 * e0, 0.007 * e0, n)], 1)
+    rel = np.stack([lin(0.2 * e0, 2 * e0, n), lin(0.02 * e0, 0.2 * e0, n), lin(0.007 * e0, 0.07 * e0, n)], 1)
+    c["reload_crossing_e_tr"] = (np.vstack([soft, unl, rel]), np.zeros(3 * n), None, dict(k_t=0.6))
+    hyd = lin(0, -6e-3, n)
+    hyd_back = lin(-6e-3, -5.5e-3, 6)[1:]
+    c["densified_unloading"] = (np.stack([np.concatenate([hyd, hyd_back]), np.zeros(n + 5), np.zeros(n + 5)], 1),
+                                np.concatenate([hyd, hyd_back]), n + 2, dict(Ed_E0=3.0))
+    c["shear_softening_H_s"] = (np.stack([lin(0, 2 * e0, n), lin(0, 12 * e0, n), lin(0, 4 * e0, n)], 1), z, 35,
+                                dict(r_s=0.2))
     return c
+
+
+def case(name):
+    """(path, eV, step index, material) of a named branch point; for the reload case the index is the
+    step that crosses e_tr (traction zero before it, positive after it)."""
+    cs = CASES[name]
+    mat = dict(MAT, **(cs[3] if len(cs) > 3 else {}))
+    path, eV, i = cs[0], cs[1], cs[2]
+    if i is None:
+        t, _ = oracle.facet_march(mat, L_FACET, path, eV)
+        teff = np.sqrt(t[:, 0] ** 2 + (t[:, 1] ** 2 + t[:, 2] ** 2) / mat["alpha"])
+        n = len(path) // 3
+        i = 2 * n + int(np.flatnonzero(teff[2 * n:] > 0)[0])
+    return path, eV, i, mat
 
 
 

@@ -14,7 +14,7 @@ import numpy as np
 import pytest
 
 import oracle
-from law_cases import CASES, IN_SCALE, L_FACET, OUT_SCALE, law_point
+from law_cases import CASES, IN_SCALE, L_FACET, OUT_SCALE, case, law_point
 from paper_2603_13190_gb300 import ldpm, specimen, workloads
 from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
 
@@ -23,31 +23,39 @@ MAT = dict(WORKLOAD_MATERIAL)
 P0 = np.array([MAT["E0"], MAT["alpha"], MAT["sigma_t"]])
 
 
-def _law_rows():
+def _law_rows(variants):
     """Rows (device layout: l, e, de, eV, t_old, e_max, E0, alpha, sigma_t, 0) at every branch point
-    and, around each, 3 random perturbations of the history and parameters within 1 %."""
+    of the given material family and, around each, 3 random perturbations of the parameters within 1 %."""
     rng = np.random.default_rng(3)
-    rows = []
+    rows, mats = [], []
     for name in sorted(CASES):
-        path, eV, i = CASES[name]
-        x = law_point(path, eV, i)
+        path, eV, i, mat = case(name)
+        if (mat != MAT) != variants:
+            continue
+        x = law_point(path, eV, i, mat)
         for r in range(4):
             y = x.copy()
             if r:
                 y[11:14] *= 1 + 0.01 * rng.uniform(-1, 1, 3)
             rows.append(np.concatenate([[L_FACET], y, [0.0]]))
-    return np.array(rows)
+            mats.append(mat)
+    return np.array(rows), mats
 
 
 @pytest.mark.parametrize("prec,tol", [(ldpm.LDPM_FP64, 1e-11), (ldpm.LDPM_MIXED, 1e-4)])
-def test_law_vjp_matches_oracle_jacobian(prec, tol):
-    rows = _law_rows()
+@pytest.mark.parametrize("variants", [False, True])
+def test_law_vjp_matches_oracle_jacobian(prec, tol, variants):
+    rows, mats = _law_rows(variants)
     rng = np.random.default_rng(5)
     aout = rng.standard_normal((len(rows), 4))
-    out, ain = ldpm.ldpm_facet_law_vjp(prec, MAT, rows, aout)
+    out = np.zeros((len(rows), 4))
+    ain = np.zeros((len(rows), 16))
+    for mat in {tuple(sorted(m.items())) for m in mats}:  # one device call per material
+        sel = [k for k, m in enumerate(mats) if tuple(sorted(m.items())) == mat]
+        out[sel], ain[sel] = ldpm.ldpm_facet_law_vjp(prec, dict(mat), rows[sel], aout[sel])
     for k, row in enumerate(rows):
         x = row[1:15]
-        mat = dict(MAT, E0=x[11], alpha=x[12], sigma_t=x[13])
+        mat = dict(mats[k], E0=x[11], alpha=x[12], sigma_t=x[13])
         o_ref, jac = oracle.facet_law_jacobian(mat, row[0], x)
         ref = aout[k] @ jac
         scale_o = np.abs(o_ref).max()

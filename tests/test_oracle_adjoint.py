@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from law_cases import CASES, IN_SCALE, L_FACET, law_point
+from law_cases import CASES, IN_SCALE, L_FACET, case, law_point
 from paper_2603_13190_gb300 import specimen, workloads
 from paper_2603_13190_gb300.specimen import Specimen
 from paper_2603_13190_gb300.workloads import WORKLOAD_MATERIAL
@@ -33,9 +33,9 @@ def _sigma_bs(tN, mat=MAT):
 
 @pytest.mark.parametrize("name", sorted(CASES))
 def test_law_jacobian_matches_central_differences(name):
-    path, eV, i = CASES[name]
-    x = law_point(path, eV, i)
-    out, jac = oracle.facet_law_jacobian(MAT, L_FACET, x)
+    path, eV, i, mat = case(name)
+    x = law_point(path, eV, i, mat)
+    out, jac = oracle.facet_law_jacobian(mat, L_FACET, x)
     # the point lies in the intended branch
     e, t_old, em_old = x[0:3], x[7:10], x[10]
     eeff = math.sqrt(e[0] ** 2 + MAT["alpha"] * (e[1] ** 2 + e[2] ** 2))
@@ -52,6 +52,12 @@ def test_law_jacobian_matches_central_differences(name):
         assert out[0] < -MAT["sigma_c0"] * 1.01
     elif name == "normal_clamped_at_zero":
         assert out[0] == 0.0 and t_old[0] < -MAT["sigma_c0"]
+    elif name == "reload_crossing_e_tr":
+        assert np.all(t_old == 0.0) and teff > 0 and out[3] > eeff
+    elif name == "densified_unloading":
+        assert -t_old[0] > MAT["sigma_c0"] and x[3] > 0
+    elif name == "shear_softening_H_s":
+        assert out[3] == eeff and teff < 0.5 * MAT["E0"] * eeff
     # central differences at two step sizes (both must agree with the Jacobian: no kink in between)
     for h in (1e-5, 1e-6):
         fd = np.zeros((4, 14))
@@ -60,7 +66,7 @@ def test_law_jacobian_matches_central_differences(name):
             xp, xm = x.copy(), x.copy()
             xp[c] += hh
             xm[c] -= hh
-            fd[:, c] = (oracle.facet_law_jacobian(MAT, L_FACET, xp)[0] - oracle.facet_law_jacobian(MAT, L_FACET, xm)[0]) / (2 * hh)
+            fd[:, c] = (oracle.facet_law_jacobian(mat, L_FACET, xp)[0] - oracle.facet_law_jacobian(mat, L_FACET, xm)[0]) / (2 * hh)
         assert np.abs(fd - jac).max() <= 1e-7 * np.abs(jac).max(), (name, h, np.abs(fd - jac).max())
 
 
