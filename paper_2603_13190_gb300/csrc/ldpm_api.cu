@@ -122,6 +122,8 @@ void law_const(const ldpm_material &mt, double dt, LawConst<R> &c)
     c.kc0 = R(mt.kc0);
     c.kc3 = R(mt.kc3);
     c.Ed_E0 = R(mt.Ed_E0);
+    c.r_s = R(mt.r_s);
+    c.k_t = R(mt.k_t);
     c.elastic = mt.elastic;
 }
 
@@ -201,12 +203,9 @@ int check_material(const ldpm_material &m)
     for (double x : v)
         if (!std::isfinite(x)) return fail(LDPM_E_INVALID_ARG, "material parameter is not finite");
     if (!(m.rho > 0 && m.E0 > 0 && m.alpha > 0 && m.sigma_t > 0 && m.l_t > 0 && m.r_st > 0 && m.n_t >= 0 &&
-          m.sigma_c0 > 0 && m.kc0 >= 1 && m.kc3 > 0 && m.sigma_N0 > 0))
-        return fail(LDPM_E_INVALID_ARG, "material: rho, E0, alpha, sigma_t, l_t, r_st, sigma_c0, kc3, sigma_N0 "
-                                        "must be > 0, n_t >= 0, kc0 >= 1");
-    if (m.k_t != 0.0) return fail(LDPM_E_UNSUPPORTED, "k_t != 0 (tensile reloading) is not implemented");
-    if (m.r_s != 0.0) return fail(LDPM_E_UNSUPPORTED, "r_s != 0 (shear cohesion softening) is not implemented");
-    if (m.Ed_E0 != 1.0) return fail(LDPM_E_UNSUPPORTED, "Ed_E0 != 1 is not implemented");
+          m.sigma_c0 > 0 && m.kc0 >= 1 && m.kc3 > 0 && m.sigma_N0 > 0 && m.Ed_E0 > 0 && m.k_t >= 0 && m.r_s >= 0))
+        return fail(LDPM_E_INVALID_ARG, "material: rho, E0, alpha, sigma_t, l_t, r_st, sigma_c0, kc3, sigma_N0, "
+                                        "Ed_E0 must be > 0; n_t, k_t, r_s >= 0; kc0 >= 1");
     if (m.reserved != 0) return fail(LDPM_E_INVALID_ARG, "material.reserved must be 0");
     return LDPM_OK;
 }

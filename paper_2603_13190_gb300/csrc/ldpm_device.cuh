@@ -66,7 +66,7 @@ __device__ __forceinline__ void tangent_frame(V3<R> n, V3<R> &m, V3<R> &l)
 }
 
 // Constants of the law for a facet with its own E0, alpha, sigma_t: the ones that depend on them are
-// rebuilt from the material's ratios (r_s = 0, so H_s / alpha = 0).
+// rebuilt from the material's ratios.
 template <class R>
 __device__ __forceinline__ LawConst<R> facet_params(const LawConst<R> &c, R E0, R alpha, R sigma_t)
 {
@@ -76,7 +76,7 @@ __device__ __forceinline__ LawConst<R> facet_params(const LawConst<R> &c, R E0, 
     p.inv_alpha = R(1) / alpha;
     p.sigma_t = sigma_t;
     p.four_alpha_over_r2 = alpha * c.four_over_r2;
-    p.Hs_over_alpha = R(0);
+    p.Hs_over_alpha = c.r_s * E0 * p.inv_alpha;
     p.Hc0 = c.Hc0_E0 * E0;
     p.Hc1 = c.Hc1_E0 * E0;
     p.ec0 = c.sigma_c0 / E0;
@@ -137,8 +137,13 @@ __device__ __forceinline__ void facet_law(const LawConst<R> &c, R l, V3<R> e, V3
         const V3<R> ep = e - de;
         const R e_old = sqrt(ep.x * ep.x + alpha * (ep.y * ep.y + ep.z * ep.z));
         const R num = de.x * (e.x + ep.x) + alpha * (de.y * (e.y + ep.y) + de.z * (e.z + ep.z));
-        const R d_eff = num / (eeff + e_old);
+        R d_eff = num / (eeff + e_old);
         const R t_old = sqrt(tN * tN + (tM * tM + tL * tL) * c.inv_alpha);
+        if (c.k_t > R(0) && t_old <= R(0) && d_eff > R(0)) {
+            // reloading from zero traction: it stays zero up to e_tr = k_t (e_max - sigma_bt / E0)
+            const R e_tr = c.k_t * (emax - sigma_bt / E0);
+            if (e_tr > e_old) d_eff = eeff > e_tr ? eeff - e_tr : R(0);
+        }
         R t = t_old + E0 * d_eff;
         t = t < R(0) ? R(0) : t;
         t = t > sigma_bt ? sigma_bt : t;

@@ -58,7 +58,8 @@ struct LawConst {
     R tiny_strain;  // fracture branch: effective strains below this respond elastically
     // ratios from which the constants above that depend on E0, alpha, sigma_t are rebuilt per facet
     // (facet_params): 4 / r_st^2, r_st, H_c0/E0, H_c1/E0, kappa_c0, kappa_c3, E_d/E0
-    R four_over_r2, r_st, Hc0_E0, Hc1_E0, kc0, kc3, Ed_E0;
+    R four_over_r2, r_st, Hc0_E0, Hc1_E0, kc0, kc3, Ed_E0, r_s;
+    R k_t;  // tensile reload: traction stays zero up to e_tr = k_t (e_max - sigma_bt / E0)
     int32_t elastic;
 };
 

@@ -84,9 +84,9 @@ def test_rejects_edge_longer_than_l_t(tet):
     _expect(-2, lambda: ldpm.ldpm_create(tet, dict(MAT, l_t=0.5)))
 
 
-@pytest.mark.parametrize("field,value,code", [("k_t", 0.5, -7), ("r_s", 0.1, -7), ("Ed_E0", 2.0, -7),
+@pytest.mark.parametrize("field,value,code", [("k_t", -0.5, -1), ("r_s", -0.1, -1), ("Ed_E0", 0.0, -1),
                                               ("E0", -1.0, -1), ("alpha", float("nan"), -1)])
-def test_rejects_unsupported_or_invalid_material(tet, field, value, code):
+def test_rejects_invalid_material(tet, field, value, code):
     _expect(code, lambda: ldpm.ldpm_create(tet, dict(MAT, **{field: value})))
 
 
@@ -101,12 +101,20 @@ def test_null_handle_calls_fail_cleanly():
     assert L.ldpm_step(None, 1) == -1
     assert L.ldpm_energy(None, None, None) == -1
     assert L.ldpm_sync(None) == -1
+    assert L.ldpm_adjoint(None, 10, 5, None, None, None, None, None) == -1
+    assert L.ldpm_set_facet_params(None, None, None, None) == -1
     L.ldpm_destroy(None)
     assert ldpm.ldpm_last_error() != ""
 
 
+def test_law_vjp_hook_rejects_bad_arguments():
+    rows, aout = np.zeros((1, 16)), np.zeros((1, 4))
+    _expect(-1, lambda: ldpm.ldpm_facet_law_vjp(5, MAT, rows, aout))
+    _expect(-1, lambda: ldpm.ldpm_facet_law_vjp(ldpm.LDPM_FP64, dict(MAT, E0=-1.0), rows, aout))
+
+
 def test_no_cpu_fallback_in_product_path():
     """The binding and package never import the oracle."""
-    for fn in ("ldpm.py", "__init__.py", "build.py", "specimen.py", "workloads.py"):
+    for fn in ("ldpm.py", "__init__.py", "build.py", "specimen.py", "workloads.py", "autograd.py"):
         src = open(os.path.join(ROOT, "paper_2603_13190_gb300", fn)).read()
         assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), fn

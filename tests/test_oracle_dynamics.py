@@ -131,3 +131,46 @@ def test_tension_energy_balance_through_softening(steps):
     assert 0 < k < len(stress) - 3, "peak must lie inside the run"
     assert stress[-1] < 0.7 * stress[k]
     assert err < 1.0
+
+
+def modal_basis(o, N):
+    """Eigenpairs of K phi = w^2 M phi (K from the oracle's elastic operator by columns, M its lumped
+    mass), phi^T M phi = 1: an independent linear-algebra route to the frequencies."""
+    import scipy.linalg
+
+    n = 6 * N
+    K = np.zeros((n, n))
+    for j in range(n):
+        q = np.zeros(n)
+        q[j] = 1.0
+        K[:, j] = -o.elastic_force(q.reshape(-1, 6)).reshape(-1)
+    K = 0.5 * (K + K.T)
+    m = o.geometry()["mass"].reshape(-1)
+    w2, phi = scipy.linalg.eigh(K, np.diag(m))
+    return np.sqrt(np.maximum(w2, 0.0)), phi, m
+
+
+def test_free_vibration_modes_follow_the_discrete_closed_form():
+    """Elastic free vibration from q = 0 with v0 = sum c_i phi_i: central difference advances each
+    mode independently, eta_i(n) = phi_i^T M q_n = (dt c_i / sin theta_i) sin(n theta_i) with
+    cos theta_i = 1 - (w_i dt)^2 / 2 (the scheme's discrete frequency, Sec. 3.2)."""
+    spec = specimen.make_cube_specimen(8.0, 2.0, 4.0, 60, seed=2)
+    mat = dict(WORKLOAD_MATERIAL, elastic=1)
+    o0 = oracle.Oracle(spec, mat, 1e-7)
+    w, phi, m = modal_basis(o0, spec.n_particles)
+    dt = 0.9 * 2.0 / w.max()
+    modes = [10, 37, len(w) - 1]
+    c = np.array([1.0, -0.5, 0.2]) * 50.0
+    v0 = (phi[:, modes] @ c).reshape(-1, 6)
+    bc = workloads.free_bc(spec.n_particles)
+    bc.v0 = v0
+    o = oracle.Oracle(spec, mat, dt, bc)
+    theta = np.arccos(1.0 - 0.5 * (w[modes] * dt) ** 2)
+    for n in range(1, 301):
+        o.step(1)
+        if n % 50:
+            continue
+        q = o.get_state()[0].reshape(-1)
+        eta = phi[:, modes].T @ (m * q)
+        expect = dt * c / np.sin(theta) * np.sin(n * theta)
+        np.testing.assert_allclose(eta, expect, rtol=0, atol=1e-9 * np.abs(dt * c / np.sin(theta)).max())
