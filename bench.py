@@ -574,16 +574,24 @@ def main():
                              "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ncu-case", choices=("mixed", "fp64"), default=None,
+    ap.add_argument("--ncu-case", choices=("mixed", "fp64", "adjoint"), default=None,
                     help="profiling target: create the workload (dt = 2e-7 s, no estimate), run 4 steps "
-                         "with plain launches and exit; nothing is timed")
+                         "with plain launches (adjoint: one 8-step ldpm_adjoint, checkpoints every 4 "
+                         "steps, on the adjoint workload in mixed precision) and exit; nothing is timed")
     args = ap.parse_args()
     if args.ncu_case:
         from paper_2603_13190_gb300 import ldpm
 
-        wl, spec, bc = make_inputs(args.workload)
-        m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=2e-7, bc=bc, graph_chunk=-1)
-        m.step(4)
+        if args.ncu_case == "adjoint":
+            wl, spec, bc = make_inputs("adjoint_uniaxial_tension")
+            m = ldpm.Model(spec, wl.material, precision="mixed", dt=2e-7, bc=bc, graph_chunk=-1)
+            seed = np.zeros((spec.n_particles, 6))
+            seed[spec.face_nodes(2, 1), 2] = 1.0
+            m.adjoint(8, seed, 4)
+        else:
+            wl, spec, bc = make_inputs(args.workload)
+            m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=2e-7, bc=bc, graph_chunk=-1)
+            m.step(4)
         m.sync()
         m.close()
         print("ncu case done: F=%d" % spec.n_facets)
