@@ -233,6 +233,14 @@ int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt);
  * at create, or the autotuner).  Library service; no counterpart in the paper. */
 int ldpm_launch_shape(ldpm_t h, int32_t shape[2]);
 
+/* Add dq [6*N] (caller particle order) to the displacements and rotations of the free DOFs of the
+ * current state; constrained DOFs are left alone.  Velocities, tractions and e_max are kept, and the
+ * next step's strain increment is measured from the perturbed state (as after ldpm_set_state).  For
+ * perturbation studies like the paper's Sec. 5 (random vectors uniform in [-eta/2, eta/2] added to
+ * all free displacements and rotations at intervals); the caller draws dq.  Synchronous.  Errors:
+ * INVALID_ARG (NULL, non-finite entries), OOM, CUDA. */
+int ldpm_perturb(ldpm_t h, const double *dq);
+
 /* ---- Per-facet parameters and the adjoint.  The paper uses one material for all facets and has no
  * derivatives; these serve sensitivity and calibration studies of its explicit step (Sec. 3,
  * App. A).  Single-specimen handles only (LDPM_E_INVALID_ARG for batches). */

@@ -61,6 +61,7 @@ def lib():
         L.orc_metrics.argtypes = [P, P, P]
         L.orc_set_bc.argtypes = [P, P, P, D]
         L.orc_set_facet_params.argtypes = [P, P, P, P]
+        L.orc_perturb.argtypes = [P, P]
         L.orc_tangent.argtypes = [P, I64, P, I32, P, P, P, P, P]
         L.orc_tangent.restype = C.c_int
         L.orc_facet_law_jacobian.argtypes = [C.POINTER(OrcMaterial), D, P, P, P]
@@ -221,6 +222,11 @@ class Oracle:
         vel = np.ascontiguousarray(bc.vel, np.float64)
         self._keep += [mask, vel]
         lib().orc_set_bc(self.h, _p(mask), _p(vel), float(bc.ramp_time))
+
+    def perturb(self, dq) -> None:
+        """q += dq [N, 6] on free DOFs; the perturbed state is the next increment's reference."""
+        dq = np.ascontiguousarray(dq, np.float64).reshape(self.N, 6)
+        lib().orc_perturb(self.h, _p(dq))
 
     def set_facet_params(self, E0=None, alpha=None, sigma_t=None) -> None:
         """Per-facet E0, alpha, sigma_t ([F] each, specimen facet order); None = material value."""

@@ -200,6 +200,7 @@ void orc_facet_march(const orc_material *p, double l, int64_t n, const double *p
 void orc_metrics(const orc_model *M, double *w, double *eV);
 void orc_set_bc(orc_model *M, const int32_t *mask, const double *vel, double ramp_time);
 void orc_set_facet_params(orc_model *M, const double *E0, const double *alpha, const double *sigma_t);
+void orc_perturb(orc_model *M, const double *dq);
 int orc_tangent(const orc_model *M, int64_t nsteps, const double *seed, int32_t nd, const double *dE0,
                 const double *dalpha, const double *dsigma_t, double *J, double *dJ);
 }
@@ -890,6 +891,17 @@ void orc_set_bc(orc_model *M, const int32_t *mask, const double *vel, double ram
         if (M->bc_mask[i] == 1) M->v[i] = 0.0;
         if (M->bc_mask[i] == 2) M->v[i] = M->bc_vel[i] * ramp(M, t);
     }
+}
+
+/* Perturbation study (Sec. 5): q += dq on the free DOFs; the strain of the perturbed state becomes
+ * the reference of the next increment (as in orc_set_state); velocities, tractions, e_max and the node
+ * forces (built from the tractions) are kept. */
+void orc_perturb(orc_model *M, const double *dq)
+{
+    size_t n6 = 6 * (size_t)M->N;
+    for (size_t i = 0; i < n6; ++i)
+        if (M->bc_mask[i] == 0) M->q[i] += dq[i];
+    for (int32_t k = 0; k < M->F; ++k) facet_strain(M, M->q, k, M->e_prev + 3 * (size_t)k);
 }
 
 /* Per-facet E0, alpha and sigma_t ([F] each, facet order of the model); a null array restores the

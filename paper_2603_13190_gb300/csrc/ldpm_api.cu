@@ -1642,6 +1642,38 @@ int ldpm_batch_info(ldpm_t h, int32_t idx, int64_t info[5], double *dt)
     return LDPM_OK;
 }
 
+int ldpm_perturb(ldpm_t h, const double *dq)
+{
+    g_err.clear();
+    if (!h || !dq) return fail(LDPM_E_INVALID_ARG, "bad handle or NULL dq");
+    DevGuard dg(h->device);
+    try {
+        std::vector<double> di(6 * (size_t)h->dm.N, 0.0);
+        size_t base = 0;
+        for (auto &S : h->sp) {
+            for (int32_t i = 0; i < S.N; ++i) {
+                const size_t P = (size_t)S.p0 + S.inv_p[i];
+                for (int k = 0; k < 6; ++k) {
+                    const double x = dq[6 * (base + i) + k];
+                    if (!std::isfinite(x)) return fail(LDPM_E_INVALID_ARG, "dq is not finite");
+                    di[6 * P + k] = x;
+                }
+            }
+            base += S.N;
+        }
+        DevArena ar;
+        double *d = nullptr;
+        int rc;
+        if ((rc = ar.get(&d, di.size()))) return rc;
+        CU(cudaMemcpyAsync(d, di.data(), di.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+        CU(launch_perturb(h->dm, d, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return LDPM_OK;
+    } catch (const std::bad_alloc &) {
+        return fail(LDPM_E_OOM, "host allocation failed");
+    }
+}
+
 int ldpm_set_facet_params(ldpm_t h, const double *E0, const double *alpha, const double *sigma_t)
 {
     g_err.clear();

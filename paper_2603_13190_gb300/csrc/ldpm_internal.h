@@ -129,6 +129,8 @@ cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s);
 // mixed mode: pm32 layout); null = the model's own.
 template <class R>
 cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s);
+// q += dq on free DOFs of the drifted state (dq [N][6] internal order, device), mirror updated.
+cudaError_t launch_perturb(const DeviceModel &m, const double *dq, cudaStream_t s);
 // Rebuild the FP32 mirror from pstate (after create, set_state, checkpoint load).  No-op in FP64.
 cudaError_t launch_mirror(const DeviceModel &m, cudaStream_t s);
 template <class R>

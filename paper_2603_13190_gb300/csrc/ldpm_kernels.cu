@@ -524,6 +524,23 @@ __global__ void __launch_bounds__(256) mirror_kernel(DeviceModel m)
     for (int k = 21; k < kMirror; ++k) pm[k] = 0.0f;
 }
 
+// Perturbation of the displacements and rotations of free DOFs (dq [N][6], internal order).  In the
+// drifted state q_{n+1} = q_n + dt v_{n+1/2}, adding dq to q_n adds it to q_{n+1}; velocities, forces
+// and history are unchanged, so the next strain increment is measured from the perturbed state.
+__global__ void __launch_bounds__(256) perturb_kernel(DeviceModel m, const double *__restrict__ dq)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * (int64_t)m.N) return;
+    const int64_t p = i / 6;
+    const int d = (int)(i - 6 * p);
+    const int mask = (int)(((uint64_t)__double_as_longlong(m.pconst[8 * p + 6]) >> (8 * d)) & 0xffu);
+    if (mask != 0) return;
+    double *ps = m.pstate + 16 * p;
+    const double q = ps[3 + d] + dq[i];
+    ps[3 + d] = q;
+    if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, q, ps[9 + d]);
+}
+
 // Energy sums over particles [p0, p1) (per block, fixed order), then one block adds the partials.
 __global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, int32_t p1, double *partial)
 {
@@ -768,6 +785,14 @@ cudaError_t launch_mirror(const DeviceModel &m, cudaStream_t s)
 {
     if (!m.pm32 || m.N == 0) return cudaSuccess;
     mirror_kernel<<<(unsigned)((m.N + 255) / 256), 256, 0, s>>>(m);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_perturb(const DeviceModel &m, const double *dq, cudaStream_t s)
+{
+    const int64_t n = 6 * (int64_t)m.N;
+    if (n == 0) return cudaSuccess;
+    perturb_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, dq);
     return cudaGetLastError();
 }
 

@@ -96,6 +96,7 @@ def lib():
             "ldpm_batch_info": ([P, I32, P, P], C.c_int),
             "ldpm_launch_shape": ([P, P], C.c_int),
             "ldpm_set_facet_params": ([P, P, P, P], C.c_int),
+            "ldpm_perturb": ([P, P], C.c_int),
             "ldpm_adjoint": ([P, I64, I32, P, P, P, P, P], C.c_int),
             "ldpm_facet_law_vjp": ([I32, P, I64, P, P, P, P], C.c_int),
         }
@@ -336,6 +337,12 @@ def ldpm_kinetic_energy_noalloc(v_dev: int, mass_dev: int, n_dof: int, out_dev: 
            "ldpm_kinetic_energy_noalloc")
 
 
+def ldpm_perturb(h, dq) -> None:
+    """Add dq [N, 6] to the free displacements and rotations of the current state."""
+    dq = np.ascontiguousarray(dq, np.float64)
+    _check(lib().ldpm_perturb(h, _ptr(dq)), "ldpm_perturb")
+
+
 def ldpm_set_facet_params(h, F: int, E0=None, alpha=None, sigma_t=None) -> None:
     """Per-facet E0 / alpha / sigma_t ([F] each, facet order; None = the material's value)."""
     arrs = [None if a is None else np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (F,)))
@@ -464,6 +471,9 @@ class Model:
 
     def info(self):
         return ldpm_info(self.h)
+
+    def perturb(self, dq):
+        ldpm_perturb(self.h, np.asarray(dq, np.float64).reshape(self.N, 6))
 
     def set_facet_params(self, E0=None, alpha=None, sigma_t=None):
         ldpm_set_facet_params(self.h, self.F, E0, alpha, sigma_t)

@@ -174,3 +174,41 @@ def test_free_vibration_modes_follow_the_discrete_closed_form():
         eta = phi[:, modes].T @ (m * q)
         expect = dt * c / np.sin(theta) * np.sin(n * theta)
         np.testing.assert_allclose(eta, expect, rtol=0, atol=1e-9 * np.abs(dt * c / np.sin(theta)).max())
+
+
+def test_rigid_perturbation_only_shifts_the_trajectory():
+    """A perturbation that is a rigid translation of the whole free specimen creates no strain: the
+    perturbed run equals the unperturbed one with q shifted by the translation; velocities and
+    tractions are unchanged (Sec. 5's perturbations act only through strains)."""
+    spec = specimen.make_cube_specimen(8.0, 2.0, 4.0, 60, seed=2)
+    rng = np.random.default_rng(1)
+    bc = workloads.free_bc(spec.n_particles)
+    bc.v0 = rng.standard_normal((spec.n_particles, 6)) * 20.0
+    a = oracle.Oracle(spec, WORKLOAD_MATERIAL, 1e-7, bc)
+    b = oracle.Oracle(spec, WORKLOAD_MATERIAL, 1e-7, bc)
+    a.step(100)
+    b.step(100)
+    shift = np.zeros((spec.n_particles, 6))
+    shift[:, :3] = [1e-3, -2e-3, 0.5e-3]
+    b.perturb(shift)
+    a.step(100)
+    b.step(100)
+    qa, va, ha, _ = a.get_state()
+    qb, vb, hb, _ = b.get_state()
+    np.testing.assert_allclose(qb - shift, qa, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(vb, va, rtol=0, atol=1e-9 * np.abs(va).max())
+    np.testing.assert_allclose(hb, ha, rtol=0, atol=1e-9 * np.abs(ha).max())
+
+
+def test_perturbation_leaves_constrained_dofs_alone():
+    spec = specimen.make_cube_specimen(8.0, 2.0, 4.0, 60, seed=2)
+    bc = workloads.uniaxial_tension_bc(spec, velocity=50.0, ramp_time=1e-5)
+    o = oracle.Oracle(spec, WORKLOAD_MATERIAL, 1e-7, bc)
+    o.step(20)
+    q0 = o.get_state()[0]
+    dq = np.full((spec.n_particles, 6), 1e-4)
+    o.perturb(dq)
+    q1 = o.get_state()[0]
+    free = bc.mask == 0
+    np.testing.assert_array_equal(q1[~free], q0[~free])
+    np.testing.assert_allclose(q1[free] - q0[free], 1e-4, rtol=1e-9)
