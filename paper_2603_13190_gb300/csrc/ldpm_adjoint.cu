@@ -38,7 +38,8 @@ struct LawVJP {
 
 // Reverse of facet_law: given the adjoints (aN, aM, aL, ah) of its outputs (t_N, t_M, t_L, e_max),
 // the adjoints of its inputs.  The forward values are recomputed with the expressions of facet_law.
-template <class R>
+// KT: the tensile reload rule may act (some k_t > 0); without it that code is compiled out.
+template <class R, bool KT>
 __device__ __forceinline__ void facet_law_vjp(const LawConst<R> &c, R l, V3<R> e, V3<R> de, R eV, R tN, R tM,
                                               R tL, R emax, R aN, R aM, R aL, R ah, LawVJP<R> &o)
 {
@@ -102,7 +103,7 @@ __device__ __forceinline__ void facet_law_vjp(const LawConst<R> &c, R l, V3<R> e
         const R t_old = sqrt(tN * tN + tT2 * c.inv_alpha);
         bool reload = false;  // k_t > 0: the increment counts only above e_tr
         R e_tr = R(0);
-        if (c.k_t > R(0) && t_old <= R(0) && d_eff > R(0)) {
+        if (KT && c.k_t > R(0) && t_old <= R(0) && d_eff > R(0)) {
             e_tr = c.k_t * (emaxp - sigma_bt / E0);
             if (e_tr > e_old) {
                 reload = true;
@@ -131,7 +132,7 @@ __device__ __forceinline__ void facet_law_vjp(const LawConst<R> &c, R l, V3<R> e
         o.gE0 += d_eff * a_tstar;
         const R a_deff = E0 * a_tstar;
         R a_emaxp = ah;
-        if (reload) {
+        if (KT && reload) {
             if (eeff > e_tr) {  // e_tr = k_t (e_max - sigma_bt / E0)
                 a_eeff += a_deff;
                 a_emaxp -= c.k_t * a_deff;
@@ -336,7 +337,7 @@ constexpr int kACon = 24;  // facet contributions: vertex a: q(6) u(6), vertex b
 // Mixed mode: 8 resident blocks per SM.  The register cap (80 per thread) costs 24 bytes of spills
 // and doubles the occupancy of the uncapped build; measured 10 % faster on GB300.  The FP64 build
 // (bound by the FP64 pipe) keeps its registers.
-template <class R>
+template <class R, bool KT>
 __global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_facet_kernel(DeviceModel m,
                                                                                             AdjointModel a)
 {
@@ -557,7 +558,7 @@ __global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_f
         const R aM = car.y - Ar * dot(mt, jf);
         const R aL = car.z - Ar * dot(lt, jf);
         LawVJP<R> o;
-        facet_law_vjp(c, l, e3, de3, seV[j], h.x, h.y, h.z, h.w, aN, aM, aL, car.w, o);
+        facet_law_vjp<R, KT>(c, l, e3, de3, seV[j], h.x, h.y, h.z, h.w, aN, aM, aL, car.w, o);
         T4 nc;
         nc.x = o.atN;
         nc.y = o.atM;
@@ -813,7 +814,7 @@ __global__ void __launch_bounds__(128) law_vjp_kernel(const LawConst<R> *law, in
     const R eV = R(x[7]);
     R tN = R(x[8]), tM = R(x[9]), tL = R(x[10]), em = R(x[11]);
     LawVJP<R> o;
-    facet_law_vjp(c, l, e, de, eV, tN, tM, tL, em, R(ao[0]), R(ao[1]), R(ao[2]), R(ao[3]), o);
+    facet_law_vjp<R, true>(c, l, e, de, eV, tN, tM, tL, em, R(ao[0]), R(ao[1]), R(ao[2]), R(ao[3]), o);
     facet_law(c, l, e, de, eV, tN, tM, tL, em);
     double *y = out + 4 * i;
     y[0] = tN;
@@ -845,7 +846,12 @@ template <class R>
 cudaError_t launch_adjoint_facet(const DeviceModel &m, const AdjointModel &a, cudaStream_t s)
 {
     const unsigned fblocks = (unsigned)((m.T + kATets - 1) / kATets);
-    if (fblocks) adjoint_facet_kernel<R><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+    if (fblocks) {
+        if (a.reload)
+            adjoint_facet_kernel<R, true><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+        else
+            adjoint_facet_kernel<R, false><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+    }
     return cudaGetLastError();
 }
 

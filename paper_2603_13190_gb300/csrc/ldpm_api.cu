@@ -1050,6 +1050,7 @@ int adjoint_run(ldpm_ctx *h, int64_t K, int64_t C, const double *seed, double *J
     DevArena ar;
     char *ckpt = nullptr, *snap = nullptr;
     AdjointModel a;
+    for (auto &sp : h->sp) a.reload |= sp.mat.k_t > 0.0;
     if ((rc = ar.get(&ckpt, stride * (size_t)(nseg + 1))) || (rc = ar.get(&snap, snap_stride * (size_t)std::min(C, K))))
         return fail(LDPM_E_OOM, "adjoint: %lld checkpoints of %zu bytes and %lld step snapshots of %zu bytes do "
                                 "not fit (use a smaller checkpoint interval)",

@@ -115,6 +115,7 @@ struct AdjointModel {
     double *Qbar = nullptr, *Ubar = nullptr, *cseed = nullptr;
     double *gsum = nullptr;  // [12T][4] FP64 totals (mixed mode: gacc is folded here per segment)
     double *jacc = nullptr;  // [N] per-particle shares of the objective, summed over the forward steps
+    int32_t reload = 0;      // 1 if some specimen has k_t > 0 (the reload rule's derivative is needed)
 };
 
 // Message returned by ldpm_last_error() on the calling thread (ldpm_api.cu).
