@@ -144,14 +144,22 @@ def dist_setup(n_gpus: int):
 
 
 def barrier_max(world: int, value: float) -> float:
+    """Maximum of `value` over the ranks (NCCL reduces device tensors, gloo host tensors)."""
     if world == 1:
         return value
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world: int, units_per_rank: float, steps: int, max_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time (weak scaling:
+    each rank steps its own replica)."""
+    return world * units_per_rank * steps / (max_ms * 1e-3)
 
 
 def barrier(world: int):
@@ -242,7 +250,7 @@ def run_ours(args, rank, world, local):
         ss_ms = e0.elapsed_time(e1) / nss
         energy, _ = model.energy()
         out[prec] = dict(
-            steps=steps, ms=ms, total_ms=tot, value=world * F * steps / (tot * 1e-3),
+            steps=steps, ms=ms, total_ms=tot, value=job_value(world, F, steps, tot),
             facet_ms=facet_ms, gather_ms=gather_ms, kick_ms=kern["kick"][0] / max(1, kern["kick"][1]),
             roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                       "traffic": recorded_traffic("facet_kernel", args.workload, prec),
@@ -349,7 +357,7 @@ def run_batch(args, rank, world, local):
     ms64, _ = time_steps(single, ldpm, torch, stream, flush, max(3, args.steps // 4), args.warmup, profile=False)
     fp64_single = specs[0].n_facets * len(ms64) / (sum(ms64) * 1e-3)
     single.close()
-    value = world * F * args.steps / (tot * 1e-3)
+    value = job_value(world, F, args.steps, tot)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": tot / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -462,7 +470,7 @@ def run_adjoint(args, rank, world, local):
     fp64_value = F * C / (a0.elapsed_time(a1) * 1e-3)
     rf64 = k64[3] / max(1, c64[3])
     fb64 = adjoint_facet_bytes(F, T, N, 8)
-    value = world * F * K / (dev_ms * 1e-3)
+    value = job_value(world, F, K, dev_ms)
     return {
         "metric": ADJ_METRIC, "value": value, "unit": "facet-updates/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak",
