@@ -253,7 +253,8 @@ def run_ours(args, rank, world, local):
             steps=steps, ms=ms, total_ms=tot, value=job_value(world, F, steps, tot),
             facet_ms=facet_ms, gather_ms=gather_ms, kick_ms=kern["kick"][0] / max(1, kern["kick"][1]),
             roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                      "traffic": recorded_traffic("facet_kernel", args.workload, prec),
+                      "traffic": recorded_traffic("facet_warp_kernel" if prec == "mixed" else "facet_kernel",
+                                                  args.workload, prec),
                       "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
             gather_roofline={"achieved": gb / (gather_ms * 1e-3) / 1e9, "frac": gb / (gather_ms * 1e-3) / 1e9 / peak,
                              "algorithmic_bytes_per_launch": gb},
