@@ -261,9 +261,10 @@ int ldpm_set_facet_params(ldpm_t h, const double *E0, const double *alpha, const
  * gives its mean reaction force), with its gradient with respect to every facet's E0, alpha and
  * sigma_t (gE0, galpha, gsigma_t: [F] each in caller facet order; any may be NULL).  The reverse
  * pass needs the states of the forward run in reverse order: the state is checkpointed on the device
- * every `ckpt_every` steps, and each segment is recomputed once, keeping its steps' inputs.  Device
- * memory: (nsteps / ckpt_every + 1) states plus ckpt_every step inputs (mixed mode: 96 B per particle
- * and 16 B per facet each).  Arithmetic in the model's precision (mixed: FP32 facet terms, FP64
+ * every `ckpt_every` steps, and each segment but the last is recomputed once, keeping its steps'
+ * inputs (the last segment's are kept during the forward run; with ckpt_every >= nsteps nothing is
+ * recomputed).  Device memory: (nsteps / ckpt_every + 1) states plus ckpt_every step inputs (mixed
+ * mode: 96 B per particle and 16 B per facet each).  Arithmetic in the model's precision (mixed: FP32 facet terms, FP64
  * particle adjoints and gradient totals).  Derivatives at points where the law is not differentiable
  * (a switch of branch, sqrt at 0) are those of the branch the forward value takes.  With gE0, galpha
  * and gsigma_t all NULL only the forward run and J are computed.  Synchronous.

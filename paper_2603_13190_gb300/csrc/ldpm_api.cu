@@ -1075,46 +1075,55 @@ int adjoint_run(ldpm_ctx *h, int64_t K, int64_t C, const double *seed, double *J
         if (objective) CU(launch_objective(h->dm, a, h->stream));
         return LDPM_OK;
     };
-    // forward sweep: checkpoint at the start of every segment, and the final state
+    const bool grads = gE0 || galpha || gsigma;
+    // keep the inputs of a step (the particle records it reads and the history before it) in slot i
+    auto keep_inputs = [&](int64_t i) -> int {
+        char *sl = snap + snap_stride * i;
+        CU(cudaMemcpyAsync(sl, mixed ? (const void *)h->dm.pm32 : (const void *)h->dm.pstate, rec,
+                           cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(sl + align256(rec), h->dm.hist, hb, cudaMemcpyDeviceToDevice, h->stream));
+        return LDPM_OK;
+    };
+    // forward sweep: checkpoint at the start of every segment, and the final state.  The last segment
+    // is the first one reversed, so its step inputs are kept now instead of being recomputed.
     for (int64_t sg = 0; sg < nseg; ++sg) {
         if ((rc = state_copy(h, ckpt + stride * sg, true))) return rc;
+        const bool last = grads && sg == nseg - 1;
         const int64_t n = std::min(C, K - sg * C);
-        for (int64_t i = 0; i < n; ++i)
+        for (int64_t i = 0; i < n; ++i) {
+            if (last && (rc = keep_inputs(i))) return rc;
             if ((rc = fwd(true))) return rc;
+        }
     }
     if ((rc = state_copy(h, ckpt + stride * nseg, true))) return rc;
     if ((rc = check_flag(h))) return rc;
-    const bool grads = gE0 || galpha || gsigma;
-    // reverse sweep
+    // reverse sweep, segment by segment from the last
     if (grads) {
-    CU(launch_adjoint_init<R>(h->dm, a, h->stream));
-    for (int64_t sg = nseg - 1; sg >= 0; --sg) {
-        if ((rc = state_copy(h, ckpt + stride * sg, false))) return rc;
-        const int64_t n = std::min(C, K - sg * C);
-        for (int64_t i = 0; i < n; ++i) {  // recompute, keeping each step's inputs
-            char *sl = snap + snap_stride * i;
-            CU(cudaMemcpyAsync(sl, mixed ? (const void *)h->dm.pm32 : (const void *)h->dm.pstate, rec,
-                               cudaMemcpyDeviceToDevice, h->stream));
-            CU(cudaMemcpyAsync(sl + align256(rec), h->dm.hist, hb, cudaMemcpyDeviceToDevice, h->stream));
-            if ((rc = fwd(false))) return rc;
+        CU(launch_adjoint_init<R>(h->dm, a, h->stream));
+        for (int64_t sg = nseg - 1; sg >= 0; --sg) {
+            const int64_t n = std::min(C, K - sg * C);
+            if (sg < nseg - 1) {  // recompute the segment from its checkpoint, keeping each step's inputs
+                if ((rc = state_copy(h, ckpt + stride * sg, false))) return rc;
+                for (int64_t i = 0; i < n; ++i)
+                    if ((rc = keep_inputs(i)) || (rc = fwd(false))) return rc;
+            }
+            for (int64_t i = n - 1; i >= 0; --i) {
+                char *sl = snap + snap_stride * i;
+                a.snap_p = sl;
+                a.snap_h = sl + align256(rec);
+                if ((rc = timed(h, 3, [&]() -> int {
+                         CU(launch_adjoint_facet<R>(h->dm, a, h->stream));
+                         return LDPM_OK;
+                     })) ||
+                    (rc = timed(h, 4, [&]() -> int {
+                         CU(launch_adjoint_gather<R>(h->dm, a, h->stream));
+                         return LDPM_OK;
+                     })))
+                    return rc;
+            }
+            if (mixed) CU(launch_adjoint_fold<R>(h->dm, a, h->stream));
         }
-        for (int64_t i = n - 1; i >= 0; --i) {
-            char *sl = snap + snap_stride * i;
-            a.snap_p = sl;
-            a.snap_h = sl + align256(rec);
-            if ((rc = timed(h, 3, [&]() -> int {
-                     CU(launch_adjoint_facet<R>(h->dm, a, h->stream));
-                     return LDPM_OK;
-                 })) ||
-                (rc = timed(h, 4, [&]() -> int {
-                     CU(launch_adjoint_gather<R>(h->dm, a, h->stream));
-                     return LDPM_OK;
-                 })))
-                return rc;
-        }
-        if (mixed) CU(launch_adjoint_fold<R>(h->dm, a, h->stream));
-    }
-    if ((rc = state_copy(h, ckpt + stride * nseg, false))) return rc;
+        if ((rc = state_copy(h, ckpt + stride * nseg, false))) return rc;
     }
     // results
     std::vector<double> jp((size_t)N);
