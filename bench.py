@@ -258,6 +258,9 @@ def run_ours(args, rank, world, local):
                       "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
             gather_roofline={"achieved": gb / (gather_ms * 1e-3) / 1e9, "frac": gb / (gather_ms * 1e-3) / 1e9 / peak,
                              "algorithmic_bytes_per_launch": gb},
+            step_roofline={"achieved": (fb + gb) / (tot / steps * 1e-3) / 1e9,
+                           "frac": (fb + gb) / (tot / steps * 1e-3) / 1e9 / peak,
+                           "algorithmic_bytes_per_step": fb + gb},
             steady_state={"facet_updates_per_s": world * F / (ss_ms * 1e-3), "ms_per_step": ss_ms,
                           "l2": "not flushed (graph replay, back-to-back)"},
             energy_err_pct=float(energy[3]), dt=model.dt)
@@ -293,10 +296,12 @@ def run_ours(args, rank, world, local):
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": wl.seed},
         "roofline": mx["roofline"],
         "gather_roofline": mx["gather_roofline"],
+        "step_roofline": mx["step_roofline"],
         "kernel_ms": {"kick": mx["kick_ms"], "facet": mx["facet_ms"], "gather": mx["gather_ms"]},
         "steady_state": mx["steady_state"],
         "fp64": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["total_ms"] / out["fp64"]["steps"],
                  "steps": out["fp64"]["steps"], "roofline": out["fp64"]["roofline"],
+                 "step_roofline": out["fp64"]["step_roofline"],
                  "kernel_ms": {"kick": out["fp64"]["kick_ms"], "facet": out["fp64"]["facet_ms"],
                                "gather": out["fp64"]["gather_ms"]},
                  "steady_state": out["fp64"]["steady_state"]},
