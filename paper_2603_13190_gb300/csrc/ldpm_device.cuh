@@ -276,6 +276,21 @@ __device__ __forceinline__ void d2f_split(double x, float &hi, float &lo)
 }
 
 // float -> double (exact for normal floats; float denormals become signed zeros).
+// Round to nearest, ties to even: the 29 dropped mantissa bits decide whether the kept 23-bit
+// mantissa is incremented (a carry out of the mantissa moves to the exponent, up to infinity).
+// Outside the normal float range it falls back to d2f_trunc.
+__device__ __forceinline__ float d2f_rn(double x)
+{
+    const uint64_t b = (uint64_t)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+    if (e <= 0 || e >= 255) return d2f_trunc(x);
+    const uint32_t m23 = (uint32_t)((b >> 29) & 0x7fffffu);
+    const uint32_t rest = (uint32_t)b & 0x1fffffffu;
+    const uint32_t u = ((uint32_t)(b >> 32) & 0x80000000u) | ((uint32_t)e << 23) | m23;
+    const bool up = rest > 0x10000000u || (rest == 0x10000000u && (m23 & 1u));
+    return __uint_as_float(u + (up ? 1u : 0u));
+}
+
 __device__ __forceinline__ double f2d_bits(float f)
 {
     const uint32_t u = __float_as_uint(f);

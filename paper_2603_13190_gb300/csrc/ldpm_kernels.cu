@@ -417,38 +417,64 @@ __global__ void __launch_bounds__(32 * WPB) facet_warp_kernel(DeviceModel m, con
 // ------------------------------------------------------------------------------------------------
 // Particle pass.  A group of LPP lanes owns one particle: it sums the particle's (tetrahedron,
 // vertex) contributions in CSR order (Eq. (2a)-(2b)), reduces across the group, and lanes 0..5 of the
-// group update one DOF each.  In mixed mode the contributions are FP32 values and their sums are
-// formed in FP32 (this adds rounding of the same order as the forces' own); everything after the sum
-// is FP64.  With LPP = 8 a
-// warp updates 4 particles per FP64 instruction: the GB300 FP64 pipe issues one warp instruction
-// per ~64 cycles per sub-partition, so FP64 instruction count, not bytes, bounds this pass if the
-// whole warp serves one particle.
+// group update one DOF each.  With LPP = 8 a warp updates 4 particles per instruction.
+// The particle's own records (mass, constraint, q, v, f_n) do not depend on the contributions and are
+// loaded before the sum, so their latency overlaps the CSR gather.
+// FP64 mode: everything after the sum is FP64.  Mixed mode: the contributions and their sums are
+// FP32, and so are the energy increments formed from them (their rounding is of the order of the FP32
+// forces'); the velocity and displacement updates are FP64 as in FP64 mode, so the trajectory is the
+// one the FP64 update of the FP32 forces gives.  The energy terms were the larger part of the FP64
+// instructions: the GB300 FP64 pipe issues one warp instruction per ~64 cycles per sub-partition.
+// The FP32 <-> FP64 conversions are integer operations.
 // ------------------------------------------------------------------------------------------------
 template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__restrict__ out6)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
     static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per particle");
     using R2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
+    constexpr bool kMixed = sizeof(R) == 4;
     const int32_t *__restrict__ ent = static_cast<const int32_t *>(m.ent);
     const R *__restrict__ tvc = static_cast<const R *>(m.tvc);
     const int lane = threadIdx.x & 31;
     const int sub = lane & (LPP - 1);
     const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
     const bool valid = p < m.N;
+    // lanes 0..5 of the group own one DOF each; the other lanes mirror DOF 0 and store nothing
+    const bool act = valid && sub < 6;
+    const int d = sub < 6 ? sub : 0;
+    const int64_t pc_ = valid ? p : 0;
     int r0 = 0, r1 = 0;
     if (valid) {
         r0 = m.row[p];
         r1 = m.row[p + 1];
     }
+    // ---- the particle's own records (step mode), issued ahead of the gather
+    double *ps = m.pstate + 16 * pc_;
+    double *pd = m.pdyn + 8 * pc_;
+    const double *pc = m.pconst + 8 * pc_;
+    const bool has_fext = m.f_ext != nullptr;
+    double im = 0.0, vh = 0.0, q0 = 0.0, fa_old = 0.0, fe = 0.0;
+    int mask = 0, sp = 0;
+    if (MODE != GATHER_ASSEMBLE) {
+        im = pc[d];
+        mask = (int)(((uint64_t)__double_as_longlong(pc[6]) >> (8 * d)) & 0xffu);
+        sp = (int)__double_as_longlong(pc[7]);
+        vh = ps[9 + d];
+        q0 = ps[3 + d];
+        fa_old = pd[d];
+        if (has_fext) fe = m.f_ext[6 * pc_ + d];
+    }
     // each entry is one (tetrahedron, vertex) slot: 6 values, force (3) and moment about the particle (3)
+    // kSlots entries per lane in flight
+    constexpr int kSlots = 2;
     R a[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-    for (int r = r0 + sub; r < r1; r += 2 * LPP) {
-        int id[2];
+    for (int r = r0 + sub; r < r1; r += kSlots * LPP) {
+        int id[kSlots];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) id[k] = (r + k * LPP < r1) ? ent[r + k * LPP] : -1;
-        R2 w[2][3];
+        for (int k = 0; k < kSlots; ++k) id[k] = (r + k * LPP < r1) ? ent[r + k * LPP] : -1;
+        R2 w[kSlots][3];
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < kSlots; ++k)
             if (id[k] >= 0) {
                 const R2 *src = reinterpret_cast<const R2 *>(tvc + 6 * (int64_t)id[k]);
                 w[k][0] = src[0];
@@ -456,7 +482,7 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
                 w[k][2] = src[2];
             }
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < kSlots; ++k)
             if (id[k] >= 0) {
                 a[0] += w[k][0].x;
                 a[1] += w[k][0].y;
@@ -470,9 +496,6 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
     for (int off = LPP / 2; off > 0; off >>= 1)
 #pragma unroll
         for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
-    // lanes 0..5 of the group own one DOF each; the other lanes mirror DOF 0 and store nothing
-    const bool act = valid && sub < 6;
-    const int d = sub < 6 ? sub : 0;
     R fr = a[0];
 #pragma unroll
     for (int k = 1; k < 6; ++k)
@@ -483,67 +506,88 @@ __global__ void __launch_bounds__(256) gather_kernel(DeviceModel m, double *__re
         return;
     }
     // ---- velocity-form central difference for DOF d (state on entry: q_{n+1}, v_{n+1/2}, f_n)
-    const int64_t pc_ = valid ? p : 0;
-    double *ps = m.pstate + 16 * pc_;
-    double *pd = m.pdyn + 8 * pc_;
-    const double *pc = m.pconst + 8 * pc_;
-    const double im = pc[d];
-    const uint64_t bcbits = (uint64_t)__double_as_longlong(pc[6]);
-    const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
-    const int sp = (int)__double_as_longlong(pc[7]);
     const SpecDyn &S = m.spec[sp];
     const double dt = S.dt, hdt = S.half_dt;
-    const bool has_fext = m.f_ext != nullptr;
-    const double fe = has_fext ? m.f_ext[6 * pc_ + d] : 0.0;
-    const double vh = ps[9 + d];
-    const double fa_old = pd[d];
     // energy terms need the external work only where a lane is constrained or loaded
     const bool need_we = __any_sync(0xffffffffu, act && (mask != 0 || has_fext));
-    double g_sum = 0.0, v_new, v_next;
-    if (mask == 0) {
-        const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
-        if (has_fext) g_sum = 2.0 * fe;
-        v_new = vh + dv;
-        v_next = v_new + dv;
-    } else if (mask == 1) {
-        g_sum = -(fa_old + fa_new);
-        v_new = 0.0;
-        v_next = 0.0;
-    } else {
-        // prescribed velocity vb ramp(t); the constraint's accelerations at t_n and t_{n+1} are
-        // vb (ramp(t +- dt/2) differences) / dt, so their sum telescopes to vb (r(t1+dt/2) - r(t0-dt/2)) / dt
+    // prescribed velocity vb ramp(t): the constraint's accelerations at t_n and t_{n+1} are
+    // vb (ramp(t +- dt/2) differences) / dt, so their sum telescopes to vb (r(t1+dt/2) - r(t0-dt/2)) / dt
+    double g_bc = 0.0, v_bc = 0.0;
+    if (mask > 1) {
         const int64_t n1 = *m.step;
         const double t1 = (double)n1 * dt;
-        const double vb = m.bc_vel[6 * pc_ + d];
         const double r_next = ramp(t1 + hdt, S.inv_ramp);
-        g_sum = m.bc_vm[6 * pc_ + d] * (r_next - ramp(t1 - dt - hdt, S.inv_ramp)) * S.inv_dt - (fa_old + fa_new);
-        v_new = vb * ramp(t1, S.inv_ramp);
-        v_next = vb * r_next;
+        g_bc = m.bc_vm[6 * pc_ + d] * (r_next - ramp(t1 - dt - hdt, S.inv_ramp)) * S.inv_dt;
+        v_bc = m.bc_vel[6 * pc_ + d] * r_next;
     }
-    // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
-    const double hdq = hdt * vh;
-    double dWi = act ? -(fa_old + fa_new) * hdq : 0.0;
-    double dWe = (need_we && act) ? g_sum * hdq : 0.0;
+    double v_next, dWi_acc, dWe_acc;
+    if constexpr (kMixed) {
+        const float f = fr;
+        const float fo = d2f_trunc(fa_old);  // exact: f_n was stored from an FP32 sum
+        const float hdt_f = d2f_rn(hdt);
+        float g = 0.0f;
+        if (mask == 0) {
+            const float fe_f = has_fext ? d2f_rn(fe) : 0.0f;
+            const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
+            if (has_fext) g = 2.0f * fe_f;
+            v_next = (vh + dv) + dv;
+        } else if (mask == 1) {
+            g = -(fo + f);
+            v_next = 0.0;
+        } else {
+            g = d2f_rn(g_bc) - (fo + f);
+            v_next = v_bc;
+        }
+        // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
+        const float hdq = hdt_f * d2f_rn(vh);
+        float dWi = act ? -(fo + f) * hdq : 0.0f;
+        float dWe = (need_we && act) ? g * hdq : 0.0f;
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
+        if (need_we) {
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
+        }
+        dWi_acc = f2d_bits(dWi);
+        dWe_acc = f2d_bits(dWe);
+    } else {
+        double g_sum = 0.0;
+        if (mask == 0) {
+            const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
+            if (has_fext) g_sum = 2.0 * fe;
+            v_next = (vh + dv) + dv;
+        } else if (mask == 1) {
+            g_sum = -(fa_old + fa_new);
+            v_next = 0.0;
+        } else {
+            g_sum = g_bc - (fa_old + fa_new);
+            v_next = v_bc;
+        }
+        // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
+        const double hdq = hdt * vh;
+        double dWi = act ? -(fa_old + fa_new) * hdq : 0.0;
+        double dWe = (need_we && act) ? g_sum * hdq : 0.0;
+        // sum the six DOF contributions into lane 0 of the group (lanes 6, 7 hold zeros)
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
+        if (need_we) {
+#pragma unroll
+            for (int off = 4; off > 0; off >>= 1) dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
+        }
+        dWi_acc = dWi;
+        dWe_acc = dWe;
+    }
     // store the drifted state of the next step: v_{n+3/2} and q_{n+2} = q_{n+1} + dt v_{n+3/2}
-    (void)v_new;
-    const double v_store = v_next;
-    const double q = ps[3 + d] + dt * v_next;
-    // sum the six DOF contributions into lane 0 of the group (lanes 6, 7 hold zeros)
-#pragma unroll
-    for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
-    if (need_we) {
-#pragma unroll
-        for (int off = 4; off > 0; off >>= 1) dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
-    }
+    const double q = q0 + dt * v_next;
     if (act) {
         pd[d] = fa_new;
         ps[3 + d] = q;
-        ps[9 + d] = v_store;
-        if (m.pm32) write_mirror(m.pm32 + kMirror * pc_, d, q, v_store);
-        if (!finite_bits(v_store) || !finite_bits(q)) *(volatile int32_t *)m.flag = 1;
+        ps[9 + d] = v_next;
+        if (m.pm32) write_mirror(m.pm32 + kMirror * pc_, d, q, v_next);
+        if (!finite_bits(v_next) || !finite_bits(q)) *(volatile int32_t *)m.flag = 1;
         if (sub == 0) {
-            pd[6] += dWi;
-            if (need_we) pd[7] += dWe;
+            pd[6] += dWi_acc;
+            if (need_we) pd[7] += dWe_acc;
         }
     }
 }
