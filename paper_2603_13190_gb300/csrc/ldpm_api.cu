@@ -16,6 +16,7 @@
 #include <numeric>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -83,6 +84,47 @@ uint32_t morton3(const double *p, const double *lo, const double *span)
         c[a] = (uint32_t)std::min(1023.0, std::floor(t * 1024.0));
     }
     return spread10(c[0]) | (spread10(c[1]) << 1) | (spread10(c[2]) << 2);
+}
+
+// fn(lo, hi) over contiguous chunks of [0, n) on up to 16 host threads; each chunk returns the first
+// index in it that failed (or hi), and the smallest of those is returned, so a check reports the same
+// index as a sequential loop would.
+template <class Fn>
+int64_t parallel_first_failure(int64_t n, Fn &&fn)
+{
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = std::max(1u, std::min(nt, 16u));
+    if (n < 65536) nt = 1;
+    if (nt == 1) return fn((int64_t)0, n);
+    std::vector<int64_t> first(nt, n);
+    std::vector<std::thread> th;
+    const int64_t chunk = (n + nt - 1) / nt;
+    try {
+        for (unsigned i = 0; i < nt; ++i) {
+            const int64_t lo = std::min(n, (int64_t)i * chunk), hi = std::min(n, lo + chunk);
+            th.emplace_back([&, i, lo, hi]() {
+                const int64_t r = fn(lo, hi);
+                first[i] = r < hi ? r : n;
+            });
+        }
+    } catch (...) {  // no thread could be started: finish on this one
+        for (auto &t : th) t.join();
+        return fn((int64_t)0, n);
+    }
+    for (auto &t : th) t.join();
+    return *std::min_element(first.begin(), first.end());
+}
+
+// Stable order of n items by 32-bit key (ties by index), as one sort of (key, index) pairs.
+std::vector<int32_t> order_by_key(const std::vector<uint32_t> &key)
+{
+    const size_t n = key.size();
+    std::vector<uint64_t> kv(n);
+    for (size_t i = 0; i < n; ++i) kv[i] = ((uint64_t)key[i] << 32) | (uint64_t)i;
+    std::sort(kv.begin(), kv.end());
+    std::vector<int32_t> perm(n);
+    for (size_t i = 0; i < n; ++i) perm[i] = (int32_t)(kv[i] & 0xffffffffu);
+    return perm;
 }
 
 template <class R>
@@ -154,6 +196,10 @@ struct ldpm_ctx {
     std::vector<double> inv_mass;  // [N][6]
     std::vector<double> pconst_h;  // [N][8]
     double *d_partial = nullptr, *d_out16 = nullptr, *h_out16 = nullptr;
+    int32_t *d_umap = nullptr;          // caller's facets of all specimens, concatenated: 2 f + orientation flip
+    std::vector<int64_t> ufoff;         // [n_spec + 1] offsets of each specimen's facets in d_umap
+    double *d_scratch = nullptr;        // state read-back scratch, grown on demand
+    size_t scratch_n = 0;
     std::map<int64_t, cudaGraphExec_t> graphs;
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -174,7 +220,7 @@ void free_model(ldpm_ctx *h)
                     h->dm.tet,
                     h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
-                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf};
+                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_out16) cudaFreeHost(h->h_out16);
@@ -265,9 +311,7 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     for (int a = 0; a < 3; ++a) span[a] = hi[a] - lo[a];
     std::vector<uint32_t> key(N);
     for (int32_t i = 0; i < N; ++i) key[i] = morton3(g.x + 3 * (size_t)i, lo, span);
-    S.perm_p.resize(N);
-    std::iota(S.perm_p.begin(), S.perm_p.end(), 0);
-    std::stable_sort(S.perm_p.begin(), S.perm_p.end(), [&](int32_t a, int32_t b) { return key[a] < key[b]; });
+    S.perm_p = order_by_key(key);
     S.inv_p.assign(N, 0);
     for (int32_t r = 0; r < N; ++r) S.inv_p[S.perm_p[r]] = r;
     std::vector<uint32_t> tkey(T);
@@ -277,9 +321,8 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
             for (int a = 0; a < 3; ++a) c[a] += 0.25 * g.x[3 * (size_t)g.tet[4 * (size_t)t + i] + a];
         tkey[t] = morton3(c, lo, span);
     }
-    std::vector<int32_t> perm_t(T), inv_t(T);
-    std::iota(perm_t.begin(), perm_t.end(), 0);
-    std::stable_sort(perm_t.begin(), perm_t.end(), [&](int32_t a, int32_t b) { return tkey[a] < tkey[b]; });
+    const std::vector<int32_t> perm_t = order_by_key(tkey);
+    std::vector<int32_t> inv_t(T);
     for (int32_t r = 0; r < T; ++r) inv_t[perm_t[r]] = r;
     S.tmap.resize(T);
     for (int32_t t = 0; t < T; ++t) S.tmap[t] = S.t0 + inv_t[t];
@@ -345,57 +388,106 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
                                             S.p0 + S.inv_p[v[3]]);
     }
     for (int32_t r = 0; r < S.T_pad / kTile; ++r) H.tile_spec[S.t0 / kTile + r] = s;
-    // ---- facets: slot = 2 * edge + k within the tetrahedron
+    // ---- facets: slot = 2 * edge + k within the tetrahedron; the first of an edge's two facets in the
+    // caller's order takes the lower slot.  Three passes: the facet's tetrahedron and edge (parallel),
+    // the slots (sequential, in the caller's order), the geometry (parallel).  Each check reports the
+    // first failing facet in the caller's order, as one sequential loop would.
     S.fmap.assign(F, -1);
     S.fswap.assign(F, 0);
-    std::vector<uint8_t> used((size_t)T * 12, 0);
-    for (int32_t k = 0; k < F; ++k) {
-        const int32_t t = g.facet_tet[k];
-        if (t < 0 || t >= T) return fail(LDPM_E_BAD_GEOMETRY, "facet %d: tetrahedron index out of range", k);
-        const int32_t *v = g.tet + 4 * (size_t)t;
-        int la = -1, lb = -1;
-        for (int i = 0; i < 4; ++i) {
-            if (v[i] == g.facet_pi[k]) la = i;
-            if (v[i] == g.facet_pj[k]) lb = i;
+    std::vector<int32_t> edge_id(F);  // 6 * (Morton rank of the tetrahedron) + edge, or -1
+    std::vector<uint8_t> lalb(F);     // local vertex indices la | lb << 2
+    int kind1 = 0;
+    const int64_t bad1 = parallel_first_failure(F, [&](int64_t lo, int64_t hi) -> int64_t {
+        for (int64_t k = lo; k < hi; ++k) {
+            const int32_t t = g.facet_tet[k];
+            if (t < 0 || t >= T) return k;
+            const int32_t *v = g.tet + 4 * (size_t)t;
+            int la = -1, lb = -1;
+            for (int i = 0; i < 4; ++i) {
+                if (v[i] == g.facet_pi[k]) la = i;
+                if (v[i] == g.facet_pj[k]) lb = i;
+            }
+            if (la < 0 || lb < 0 || la == lb) return k;
+            edge_id[k] = 6 * inv_t[t] + edge_of(la, lb);
+            lalb[k] = (uint8_t)(la | (lb << 2));
         }
-        if (la < 0 || lb < 0 || la == lb)
-            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: I and J must be two vertices of its tetrahedron", k);
-        const int e = edge_of(la, lb);
-        const int32_t rt = inv_t[t];
-        int slot = 2 * e;
+        return hi;
+    });
+    if (bad1 < F) {
+        const int32_t t = g.facet_tet[bad1];
+        kind1 = (t < 0 || t >= T) ? 1 : 2;
+    }
+    std::vector<uint8_t> used((size_t)T * 12, 0);
+    int64_t bad2 = F;
+    for (int64_t k = 0; k < bad1; ++k) {
+        const int64_t e6 = edge_id[k];
+        const int64_t rt = e6 / 6;
+        int slot = 2 * (int)(e6 - 6 * rt);
         if (used[(size_t)rt * 12 + slot]) ++slot;
-        if (used[(size_t)rt * 12 + slot])
-            return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: more than 2 facets on one edge", t);
+        if (used[(size_t)rt * 12 + slot]) {
+            bad2 = k;
+            break;
+        }
         used[(size_t)rt * 12 + slot] = 1;
-        const int64_t fi = ((int64_t)S.t0 + rt) * 12 + slot;
-        S.fmap[k] = fi;
-        S.fswap[k] = la > lb;
-        // geometry from the internal first vertex a = min(la, lb)
-        const int32_t pa = v[std::min(la, lb)], pb = v[std::max(la, lb)];
-        const double *xa = g.x + 3 * (size_t)pa, *xb = g.x + 3 * (size_t)pb;
+        S.fmap[k] = ((int64_t)S.t0 + rt) * 12 + slot;
+        S.fswap[k] = (lalb[k] & 3) > (lalb[k] >> 2);
+    }
+    const int64_t upto = std::min(bad1, bad2);
+    const int64_t bad3 = parallel_first_failure(upto, [&](int64_t lo, int64_t hi) -> int64_t {
+        for (int64_t k = lo; k < hi; ++k) {
+            const int32_t *v = g.tet + 4 * (size_t)g.facet_tet[k];
+            const int la = lalb[k] & 3, lb = lalb[k] >> 2;
+            const int64_t fi = S.fmap[k];
+            // geometry from the internal first vertex a = min(la, lb)
+            const int32_t pa = v[std::min(la, lb)], pb = v[std::max(la, lb)];
+            const double *xa = g.x + 3 * (size_t)pa, *xb = g.x + 3 * (size_t)pb;
+            const double *p0 = g.facet_vtx + 9 * (size_t)k;
+            double dd[3], e1[3], e2[3], xc[3];
+            for (int a = 0; a < 3; ++a) {
+                dd[a] = xb[a] - xa[a];
+                e1[a] = p0[3 + a] - p0[a];
+                e2[a] = p0[6 + a] - p0[a];
+                xc[a] = (p0[a] + p0[3 + a] + p0[6 + a]) / 3.0;
+            }
+            const double l = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+            const double nc[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                                  e1[0] * e2[1] - e1[1] * e2[0]};
+            const double twoA0 = std::sqrt(nc[0] * nc[0] + nc[1] * nc[1] + nc[2] * nc[2]);
+            if (!(l > 0) || !(twoA0 > 0) || !std::isfinite(twoA0)) return k;
+            if (!(l < mat.l_t)) return k;
+            // projected area A = A0 |n . n0| (Sec. 2)
+            const double A = 0.5 * std::fabs((dd[0] * nc[0] + dd[1] * nc[1] + dd[2] * nc[2]) / l);
+            for (int a = 0; a < 3; ++a) H.geo64[4 * (size_t)fi + a] = xc[a] - xa[a];
+            H.geo64[4 * (size_t)fi + 3] = A;
+        }
+        return hi;
+    });
+    if (bad3 < upto) {  // the same two checks again, for the message
+        const int64_t k = bad3;
+        const int32_t *v = g.tet + 4 * (size_t)g.facet_tet[k];
+        const int la = lalb[k] & 3, lb = lalb[k] >> 2;
+        const double *xa = g.x + 3 * (size_t)v[std::min(la, lb)], *xb = g.x + 3 * (size_t)v[std::max(la, lb)];
         const double *p0 = g.facet_vtx + 9 * (size_t)k;
-        double dd[3], e1[3], e2[3], xc[3];
+        double l2 = 0.0, e1[3], e2[3];
         for (int a = 0; a < 3; ++a) {
-            dd[a] = xb[a] - xa[a];
+            l2 += (xb[a] - xa[a]) * (xb[a] - xa[a]);
             e1[a] = p0[3 + a] - p0[a];
             e2[a] = p0[6 + a] - p0[a];
-            xc[a] = (p0[a] + p0[3 + a] + p0[6 + a]) / 3.0;
         }
-        const double l = std::sqrt(dd[0] * dd[0] + dd[1] * dd[1] + dd[2] * dd[2]);
+        const double l = std::sqrt(l2);
         const double nc[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
                               e1[0] * e2[1] - e1[1] * e2[0]};
         const double twoA0 = std::sqrt(nc[0] * nc[0] + nc[1] * nc[1] + nc[2] * nc[2]);
         if (!(l > 0) || !(twoA0 > 0) || !std::isfinite(twoA0))
-            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: zero edge length or facet area", k);
-        if (!(l < mat.l_t))
-            return fail(LDPM_E_BAD_GEOMETRY, "facet %d: edge length %g >= l_t (softening modulus undefined)", k, l);
-        // projected area A = A0 |n . n0| (Sec. 2)
-        const double A = 0.5 * std::fabs((dd[0] * nc[0] + dd[1] * nc[1] + dd[2] * nc[2]) / l);
-        for (int a = 0; a < 3; ++a) {
-            H.geo64[4 * (size_t)fi + a] = xc[a] - xa[a];
-        }
-        H.geo64[4 * (size_t)fi + 3] = A;
+            return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: zero edge length or facet area", (long long)k);
+        return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: edge length %g >= l_t (softening modulus undefined)",
+                    (long long)k, l);
     }
+    if (bad2 < bad1)
+        return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: more than 2 facets on one edge", g.facet_tet[bad2]);
+    if (kind1 == 1) return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: tetrahedron index out of range", (long long)bad1);
+    if (kind1 == 2)
+        return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: I and J must be two vertices of its tetrahedron", (long long)bad1);
     for (int32_t r = 0; r < T; ++r)
         for (int sl = 0; sl < 12; ++sl)
             if (!used[(size_t)r * 12 + sl])
@@ -722,6 +814,15 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
             for (int k = 0; k < 4; ++k) H.ent_id[pos[vv[k]]++] = 4 * t + k;
         }
     }
+    // ---- caller's facet order -> internal facet (with the orientation flip in bit 0)
+    std::vector<int32_t> umap;
+    h->ufoff.assign(n + 1, 0);
+    for (int s = 0; s < n; ++s) h->ufoff[s + 1] = h->ufoff[s] + h->sp[s].F;
+    umap.resize((size_t)h->ufoff[n]);
+    for (int s = 0; s < n; ++s) {
+        const SpecHost &S = h->sp[s];
+        for (int32_t k = 0; k < S.F; ++k) umap[(size_t)h->ufoff[s] + k] = (int32_t)(2 * S.fmap[k] + S.fswap[k]);
+    }
     // ---- device
     int dev = o0.device;
     if (dev < 0) CU(cudaGetDevice(&dev));
@@ -765,8 +866,9 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         (rc = dalloc(&dm.tet, (size_t)T)) || (rc = dalloc(&dm.row, (size_t)N + 1)) ||
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
-        (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))))
+        (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())))
         return rc;
+    CU(cudaMemcpy(h->d_umap, umap.data(), umap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (H.any_fext) {
         if ((rc = dalloc(&dm.f_ext, 6 * (size_t)N))) return rc;
         CU(cudaMemcpy(dm.f_ext, H.f_ext.data(), H.f_ext.size() * sizeof(double), cudaMemcpyHostToDevice));
@@ -938,28 +1040,27 @@ struct DevGuard {
 };
 
 // Caller-order state <-> internal arrays.
-int download_state(ldpm_ctx *h, std::vector<double> &ps, std::vector<double> *hist5_int)
+int download_state(ldpm_ctx *h, std::vector<double> &ps)
 {
     ps.resize(16 * (size_t)h->dm.N);
     CU(cudaMemcpyAsync(ps.data(), h->dm.pstate, ps.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    if (hist5_int) {
-        const int64_t Fint = 12 * (int64_t)h->dm.T;
-        double *d5 = nullptr;
-        int rc;
-        if ((rc = dalloc(&d5, 5 * (size_t)Fint))) return rc;
-        cudaError_t e = h->prec == LDPM_MIXED ? launch_hist_to_user<float>(h->dm, d5, h->stream)
-                                              : launch_hist_to_user<double>(h->dm, d5, h->stream);
-        hist5_int->resize(5 * (size_t)Fint);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(hist5_int->data(), d5, hist5_int->size() * sizeof(double), cudaMemcpyDeviceToHost,
-                                h->stream);
-        cudaError_t e2 = cudaStreamSynchronize(h->stream);
-        cudaFree(d5);
-        if (e != cudaSuccess || e2 != cudaSuccess)
-            return fail(LDPM_E_CUDA, "history download: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-    }
     CU(cudaStreamSynchronize(h->stream));
     return LDPM_OK;
+}
+
+// Device scratch of at least n doubles, kept until the handle is destroyed.
+int scratch(ldpm_ctx *h, size_t n)
+{
+    if (h->scratch_n >= n) return LDPM_OK;
+    if (h->d_scratch) {
+        CU(cudaStreamSynchronize(h->stream));
+        cudaFree(h->d_scratch);
+        h->d_scratch = nullptr;
+        h->scratch_n = 0;
+    }
+    int rc = dalloc(&h->d_scratch, n);
+    if (rc == LDPM_OK) h->scratch_n = n;
+    return rc;
 }
 
 // ---- per-facet parameters and the adjoint -------------------------------------------------------
@@ -1209,23 +1310,26 @@ static int get_state_range(ldpm_t h, int s_lo, int s_hi, double *q, double *v, d
 {
     DevGuard dg(h->device);
     try {
-        std::vector<double> ps, h5;
-        int rc = download_state(h, ps, hist5 ? &h5 : nullptr);
-        if (rc) return rc;
-        // whole-step q_n, v_n from the drifted state
-        std::vector<double> qv(12 * (size_t)h->dm.N);
-        double *d12 = nullptr;
-        if ((rc = dalloc(&d12, qv.size()))) return rc;
-        cudaError_t e = launch_unkick(h->dm, d12, h->stream);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(qv.data(), d12, qv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-        cudaError_t e2 = cudaStreamSynchronize(h->stream);
-        cudaFree(d12);
-        if (e != cudaSuccess || e2 != cudaSuccess)
-            return fail(LDPM_E_CUDA, "state read-back: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+        // whole-step q_n, v_n from the drifted state; the history is converted and put in the caller's
+        // facet order on the device and copied straight into hist5
+        const size_t N = (size_t)h->dm.N;
+        const int64_t k0 = h->ufoff[s_lo], k1 = h->ufoff[s_hi];
+        int rc;
+        if ((rc = scratch(h, 12 * N + (hist5 ? 5 * (size_t)(k1 - k0) : 0)))) return rc;
+        double *d12 = h->d_scratch, *d5 = h->d_scratch + 12 * N;
+        std::vector<double> qv(12 * N);
+        CU(launch_unkick(h->dm, d12, h->stream));
+        CU(cudaMemcpyAsync(qv.data(), d12, qv.size() * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        if (hist5) {
+            CU(h->prec == LDPM_MIXED ? launch_hist_to_user<float>(h->dm, h->d_umap + k0, k1 - k0, d5, h->stream)
+                                     : launch_hist_to_user<double>(h->dm, h->d_umap + k0, k1 - k0, d5, h->stream));
+            CU(cudaMemcpyAsync(hist5, d5, 5 * (size_t)(k1 - k0) * sizeof(double), cudaMemcpyDeviceToHost,
+                               h->stream));
+        }
         int64_t st = 0;
-        CU(cudaMemcpy(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost));
-        size_t base_p = 0, base_f = 0;
+        CU(cudaMemcpyAsync(&st, h->dm.step, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        size_t base_p = 0;
         for (int si = s_lo; si < s_hi; ++si) {
             const SpecHost &S = h->sp[si];
             for (int32_t i = 0; i < S.N; ++i) {
@@ -1235,19 +1339,7 @@ static int get_state_range(ldpm_t h, int s_lo, int s_hi, double *q, double *v, d
                     if (v) v[6 * (base_p + i) + k] = qv[12 * P + 6 + k];
                 }
             }
-            if (hist5)
-                for (int32_t k = 0; k < S.F; ++k) {
-                    const double *src = &h5[5 * (size_t)S.fmap[k]];
-                    double *dst = hist5 + 5 * (base_f + k);
-                    const double sg = S.fswap[k] ? -1.0 : 1.0;
-                    dst[0] = src[0];
-                    dst[1] = sg * src[1];
-                    dst[2] = sg * src[2];
-                    dst[3] = sg * src[3];
-                    dst[4] = src[4];
-                }
             base_p += S.N;
-            base_f += S.F;
         }
         if (step) *step = st;
         return check_flag(h);
@@ -1271,7 +1363,7 @@ int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *his
     DevGuard dg(h->device);
     try {
         std::vector<double> ps;
-        int rc = download_state(h, ps, nullptr);
+        int rc = download_state(h, ps);
         if (rc) return rc;
         const int64_t Fint = 12 * (int64_t)h->dm.T;
         std::vector<double> h5(5 * (size_t)Fint, 0.0);

@@ -140,8 +140,10 @@ cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStre
 // reaction prescribed(6).  `partial` holds ceil((p1 - p0) / 256) * 16 doubles.
 cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, double *out16,
                           cudaStream_t s);
+// History of n facets in the caller's order (out5 [n][5]: t_N, tangential traction vector, e_max);
+// umap[k] = 2 f + s, f the internal facet, s = 1 where the caller's facet has the opposite orientation.
 template <class R>
-cudaError_t launch_hist_to_user(const DeviceModel &m, double *out5, cudaStream_t s);
+cudaError_t launch_hist_to_user(const DeviceModel &m, const int32_t *umap, int64_t n, double *out5, cudaStream_t s);
 
 // Adjoint launchers (ldpm_adjoint.cu).
 // Reset: af = c, Qbar = Ubar = 0, adj_h = 0, gacc = 0 (and gsum = 0).

@@ -791,22 +791,28 @@ __device__ __forceinline__ bool facet_frame_of(const DeviceModel &m, int64_t f, 
     return true;
 }
 
+// History of n facets in the caller's order: umap[k] = 2 f + s for internal facet f, s = 1 where the
+// caller's facet runs from the internal vertex b to a (the tangential traction vector flips sign).
 template <class R>
-__global__ void hist_to_user_kernel(DeviceModel m, double *__restrict__ out5)
+__global__ void hist_to_user_kernel(DeviceModel m, const int32_t *__restrict__ umap, int64_t nf,
+                                    double *__restrict__ out5)
 {
-    const int64_t f = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (f >= 12 * (int64_t)m.T) return;
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nf) return;
+    const int32_t code = umap[k];
+    const int64_t f = code >> 1;
+    const double sg = (code & 1) ? -1.0 : 1.0;
     V3<R> n, mt, lt;
     const R4<R> h = static_cast<const R4<R> *>(m.hist)[f];
-    double *o = out5 + 5 * f;
+    double *o = out5 + 5 * k;
     if (!facet_frame_of<R>(m, f, n, mt, lt)) {
-        for (int k = 0; k < 5; ++k) o[k] = 0.0;
+        for (int c = 0; c < 5; ++c) o[c] = 0.0;
         return;
     }
     o[0] = double(h.x);
-    o[1] = double(h.y) * double(mt.x) + double(h.z) * double(lt.x);
-    o[2] = double(h.y) * double(mt.y) + double(h.z) * double(lt.y);
-    o[3] = double(h.y) * double(mt.z) + double(h.z) * double(lt.z);
+    o[1] = sg * (double(h.y) * double(mt.x) + double(h.z) * double(lt.x));
+    o[2] = sg * (double(h.y) * double(mt.y) + double(h.z) * double(lt.y));
+    o[3] = sg * (double(h.y) * double(mt.z) + double(h.z) * double(lt.z));
     o[4] = double(h.w);
 }
 
@@ -958,11 +964,10 @@ cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *
 }
 
 template <class R>
-cudaError_t launch_hist_to_user(const DeviceModel &m, double *out5, cudaStream_t s)
+cudaError_t launch_hist_to_user(const DeviceModel &m, const int32_t *umap, int64_t n, double *out5, cudaStream_t s)
 {
-    const int64_t n = 12 * (int64_t)m.T;
-    if (n == 0) return cudaSuccess;
-    hist_to_user_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, out5);
+    if (n <= 0) return cudaSuccess;
+    hist_to_user_kernel<R><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, umap, n, out5);
     return cudaGetLastError();
 }
 
@@ -979,8 +984,8 @@ template cudaError_t launch_facet<float>(const DeviceModel &, int, const void *,
 template cudaError_t launch_facet<double>(const DeviceModel &, int, const void *, cudaStream_t);
 template cudaError_t launch_gather<float>(const DeviceModel &, int, double *, cudaStream_t);
 template cudaError_t launch_gather<double>(const DeviceModel &, int, double *, cudaStream_t);
-template cudaError_t launch_hist_to_user<float>(const DeviceModel &, double *, cudaStream_t);
-template cudaError_t launch_hist_to_user<double>(const DeviceModel &, double *, cudaStream_t);
+template cudaError_t launch_hist_to_user<float>(const DeviceModel &, const int32_t *, int64_t, double *, cudaStream_t);
+template cudaError_t launch_hist_to_user<double>(const DeviceModel &, const int32_t *, int64_t, double *, cudaStream_t);
 template cudaError_t launch_hist_from_user<float>(const DeviceModel &, const double *, cudaStream_t);
 template cudaError_t launch_hist_from_user<double>(const DeviceModel &, const double *, cudaStream_t);
 
