@@ -86,45 +86,54 @@ uint32_t morton3(const double *p, const double *lo, const double *span)
     return spread10(c[0]) | (spread10(c[1]) << 1) | (spread10(c[2]) << 2);
 }
 
-// fn(lo, hi) over contiguous chunks of [0, n) on up to 16 host threads; each chunk returns the first
-// index in it that failed (or hi), and the smallest of those is returned, so a check reports the same
-// index as a sequential loop would.
+// fn(lo, hi) over contiguous chunks of [0, n) on up to 16 host threads (one thread below 65536
+// items); returns the smallest of the chunks' results.  The checks below return the first failing
+// item of their chunk (or a sentinel), so the result is the item a sequential loop would report.
 template <class Fn>
-int64_t parallel_first_failure(int64_t n, Fn &&fn)
+int64_t parallel_min(int64_t n, Fn &&fn)
 {
     unsigned nt = std::thread::hardware_concurrency();
     nt = std::max(1u, std::min(nt, 16u));
     if (n < 65536) nt = 1;
     if (nt == 1) return fn((int64_t)0, n);
-    std::vector<int64_t> first(nt, n);
+    std::vector<int64_t> res(nt, INT64_MAX);
     std::vector<std::thread> th;
     const int64_t chunk = (n + nt - 1) / nt;
     try {
         for (unsigned i = 0; i < nt; ++i) {
             const int64_t lo = std::min(n, (int64_t)i * chunk), hi = std::min(n, lo + chunk);
-            th.emplace_back([&, i, lo, hi]() {
-                const int64_t r = fn(lo, hi);
-                first[i] = r < hi ? r : n;
-            });
+            th.emplace_back([&, i, lo, hi]() { res[i] = fn(lo, hi); });
         }
     } catch (...) {  // no thread could be started: finish on this one
         for (auto &t : th) t.join();
         return fn((int64_t)0, n);
     }
     for (auto &t : th) t.join();
-    return *std::min_element(first.begin(), first.end());
+    return *std::min_element(res.begin(), res.end());
 }
 
-// Stable order of n items by 32-bit key (ties by index), as one sort of (key, index) pairs.
+// Stable order of n items by 32-bit key (ties by index): LSD radix sort of (key, index) pairs, 8 bits
+// per pass.
 std::vector<int32_t> order_by_key(const std::vector<uint32_t> &key)
 {
     const size_t n = key.size();
-    std::vector<uint64_t> kv(n);
-    for (size_t i = 0; i < n; ++i) kv[i] = ((uint64_t)key[i] << 32) | (uint64_t)i;
-    std::sort(kv.begin(), kv.end());
-    std::vector<int32_t> perm(n);
-    for (size_t i = 0; i < n; ++i) perm[i] = (int32_t)(kv[i] & 0xffffffffu);
-    return perm;
+    std::vector<uint32_t> ka(key), kb(n);
+    std::vector<int32_t> ia(n), ib(n);
+    std::iota(ia.begin(), ia.end(), 0);
+    for (int sh = 0; sh < 32; sh += 8) {
+        size_t cnt[257] = {0};
+        for (size_t i = 0; i < n; ++i) ++cnt[((ka[i] >> sh) & 0xffu) + 1];
+        if (cnt[((ka.empty() ? 0 : ka[0]) >> sh & 0xffu) + 1] == n) continue;  // one digit value: order kept
+        for (int d = 0; d < 256; ++d) cnt[d + 1] += cnt[d];
+        for (size_t i = 0; i < n; ++i) {
+            const size_t pos = cnt[(ka[i] >> sh) & 0xffu]++;
+            kb[pos] = ka[i];
+            ib[pos] = ia[i];
+        }
+        ka.swap(kb);
+        ia.swap(ib);
+    }
+    return ia;
 }
 
 template <class R>
@@ -261,7 +270,7 @@ int check_material(const ldpm_material &m)
 struct HostArrays {
     std::vector<double> pstate, pdyn, pconst, bc_vel, bc_vm, f_ext;
     std::vector<int4> tet;
-    std::vector<double> geo64;  // [Fint][4] before rounding to R
+    std::unique_ptr<double[]> geo64;  // [Fint][4] before rounding to R (padding facets zeroed)
     std::vector<int32_t> row;
     std::vector<int64_t> ent_id;  // CSR payload: tetrahedron vertex slot 4 * tet + vertex
     std::vector<int32_t> tile_spec;
@@ -315,12 +324,15 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     S.inv_p.assign(N, 0);
     for (int32_t r = 0; r < N; ++r) S.inv_p[S.perm_p[r]] = r;
     std::vector<uint32_t> tkey(T);
-    for (int32_t t = 0; t < T; ++t) {
-        double c[3] = {0, 0, 0};
-        for (int i = 0; i < 4; ++i)
-            for (int a = 0; a < 3; ++a) c[a] += 0.25 * g.x[3 * (size_t)g.tet[4 * (size_t)t + i] + a];
-        tkey[t] = morton3(c, lo, span);
-    }
+    parallel_min(T, [&](int64_t t0, int64_t t1) -> int64_t {
+        for (int64_t t = t0; t < t1; ++t) {
+            double c[3] = {0, 0, 0};
+            for (int i = 0; i < 4; ++i)
+                for (int a = 0; a < 3; ++a) c[a] += 0.25 * g.x[3 * (size_t)g.tet[4 * (size_t)t + i] + a];
+            tkey[t] = morton3(c, lo, span);
+        }
+        return 0;
+    });
     const std::vector<int32_t> perm_t = order_by_key(tkey);
     std::vector<int32_t> inv_t(T);
     for (int32_t r = 0; r < T; ++r) inv_t[perm_t[r]] = r;
@@ -394,10 +406,10 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     // first failing facet in the caller's order, as one sequential loop would.
     S.fmap.assign(F, -1);
     S.fswap.assign(F, 0);
-    std::vector<int32_t> edge_id(F);  // 6 * (Morton rank of the tetrahedron) + edge, or -1
-    std::vector<uint8_t> lalb(F);     // local vertex indices la | lb << 2
+    std::vector<int32_t> rank(F);  // Morton rank of the facet's tetrahedron
+    std::vector<uint8_t> lalb(F);  // local vertex indices la | lb << 2, edge << 4
     int kind1 = 0;
-    const int64_t bad1 = parallel_first_failure(F, [&](int64_t lo, int64_t hi) -> int64_t {
+    const int64_t bad1 = parallel_min(F, [&](int64_t lo, int64_t hi) -> int64_t {
         for (int64_t k = lo; k < hi; ++k) {
             const int32_t t = g.facet_tet[k];
             if (t < 0 || t >= T) return k;
@@ -408,35 +420,40 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
                 if (v[i] == g.facet_pj[k]) lb = i;
             }
             if (la < 0 || lb < 0 || la == lb) return k;
-            edge_id[k] = 6 * inv_t[t] + edge_of(la, lb);
-            lalb[k] = (uint8_t)(la | (lb << 2));
+            rank[k] = inv_t[t];
+            lalb[k] = (uint8_t)(la | (lb << 2) | (edge_of(la, lb) << 4));
         }
-        return hi;
+        return (int64_t)F;
     });
     if (bad1 < F) {
         const int32_t t = g.facet_tet[bad1];
         kind1 = (t < 0 || t >= T) ? 1 : 2;
     }
+    // Facets compete for slots only within their tetrahedron: each thread owns a range of Morton
+    // ranks and scans all facets in the caller's order, taking those of its tetrahedra.
     std::vector<uint8_t> used((size_t)T * 12, 0);
-    int64_t bad2 = F;
-    for (int64_t k = 0; k < bad1; ++k) {
-        const int64_t e6 = edge_id[k];
-        const int64_t rt = e6 / 6;
-        int slot = 2 * (int)(e6 - 6 * rt);
-        if (used[(size_t)rt * 12 + slot]) ++slot;
-        if (used[(size_t)rt * 12 + slot]) {
-            bad2 = k;
-            break;
+    const int64_t bad2 = parallel_min(T, [&](int64_t r0, int64_t r1) -> int64_t {
+        int64_t first = bad1;
+        for (int64_t k = 0; k < bad1; ++k) {
+            const int64_t rt = rank[k];
+            if (rt < r0 || rt >= r1) continue;
+            int slot = 2 * (lalb[k] >> 4);
+            if (used[(size_t)rt * 12 + slot]) ++slot;
+            if (used[(size_t)rt * 12 + slot]) {
+                first = k;
+                break;
+            }
+            used[(size_t)rt * 12 + slot] = 1;
+            S.fmap[k] = ((int64_t)S.t0 + rt) * 12 + slot;
+            S.fswap[k] = (lalb[k] & 3) > ((lalb[k] >> 2) & 3);
         }
-        used[(size_t)rt * 12 + slot] = 1;
-        S.fmap[k] = ((int64_t)S.t0 + rt) * 12 + slot;
-        S.fswap[k] = (lalb[k] & 3) > (lalb[k] >> 2);
-    }
+        return first;
+    });
     const int64_t upto = std::min(bad1, bad2);
-    const int64_t bad3 = parallel_first_failure(upto, [&](int64_t lo, int64_t hi) -> int64_t {
+    const int64_t bad3 = parallel_min(upto, [&](int64_t lo, int64_t hi) -> int64_t {
         for (int64_t k = lo; k < hi; ++k) {
             const int32_t *v = g.tet + 4 * (size_t)g.facet_tet[k];
-            const int la = lalb[k] & 3, lb = lalb[k] >> 2;
+            const int la = lalb[k] & 3, lb = (lalb[k] >> 2) & 3;
             const int64_t fi = S.fmap[k];
             // geometry from the internal first vertex a = min(la, lb)
             const int32_t pa = v[std::min(la, lb)], pb = v[std::max(la, lb)];
@@ -460,12 +477,12 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
             for (int a = 0; a < 3; ++a) H.geo64[4 * (size_t)fi + a] = xc[a] - xa[a];
             H.geo64[4 * (size_t)fi + 3] = A;
         }
-        return hi;
+        return upto;
     });
     if (bad3 < upto) {  // the same two checks again, for the message
         const int64_t k = bad3;
         const int32_t *v = g.tet + 4 * (size_t)g.facet_tet[k];
-        const int la = lalb[k] & 3, lb = lalb[k] >> 2;
+        const int la = lalb[k] & 3, lb = (lalb[k] >> 2) & 3;
         const double *xa = g.x + 3 * (size_t)v[std::min(la, lb)], *xb = g.x + 3 * (size_t)v[std::max(la, lb)];
         const double *p0 = g.facet_vtx + 9 * (size_t)k;
         double l2 = 0.0, e1[3], e2[3];
@@ -500,12 +517,15 @@ int upload_facets(ldpm_ctx *h, const HostArrays &H, int64_t Fint)
 {
     using T4 = R4<R>;
     std::vector<T4> geo(Fint);
-    for (int64_t f = 0; f < Fint; ++f) {
-        geo[f].x = R(H.geo64[4 * f]);
-        geo[f].y = R(H.geo64[4 * f + 1]);
-        geo[f].z = R(H.geo64[4 * f + 2]);
-        geo[f].w = R(H.geo64[4 * f + 3]);
-    }
+    parallel_min(Fint, [&](int64_t f0, int64_t f1) -> int64_t {
+        for (int64_t f = f0; f < f1; ++f) {
+            geo[f].x = R(H.geo64[4 * f]);
+            geo[f].y = R(H.geo64[4 * f + 1]);
+            geo[f].z = R(H.geo64[4 * f + 2]);
+            geo[f].w = R(H.geo64[4 * f + 3]);
+        }
+        return 0;
+    });
     const int64_t nent = H.ent_id.size();
     std::vector<int32_t> ent(nent);
     for (int64_t r = 0; r < nent; ++r) ent[r] = (int32_t)H.ent_id[r];
@@ -783,7 +803,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     H.bc_vm.assign(6 * (size_t)N, 0.0);
     H.f_ext.assign(6 * (size_t)N, 0.0);
     H.tet.assign(T, make_int4(-1, -1, -1, -1));
-    H.geo64.assign(4 * (size_t)Fint, 0.0);
+    H.geo64.reset(new double[4 * (size_t)Fint]);  // every facet of a real tetrahedron is written
     H.tile_spec.assign(T / kTile, 0);
     h->x_int.assign(3 * (size_t)N, 0.0);
     h->inv_mass.assign(6 * (size_t)N, 0.0);
@@ -791,6 +811,8 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     for (int s = 0; s < n; ++s) {
         int rc = prepare_specimen(s, geoms[s], opts[s], h->sp[s], H, h->x_int, h->inv_mass, h->pconst_h);
         if (rc) return rc;
+        const SpecHost &S = h->sp[s];
+        std::fill(H.geo64.get() + 48 * ((size_t)S.t0 + S.T), H.geo64.get() + 48 * ((size_t)S.t0 + S.T_pad), 0.0);
     }
     // ---- CSR of facet ends, ascending facet id within each particle (fixed summation order)
     H.row.assign((size_t)N + 1, 0);
