@@ -205,6 +205,7 @@ struct ldpm_ctx {
     std::vector<double> inv_mass;  // [N][6]
     std::vector<double> pconst_h;  // [N][8]
     double *d_partial = nullptr, *d_out16 = nullptr, *h_out16 = nullptr;
+    unsigned *d_ticket = nullptr;       // block counter of the energy reduction
     int32_t *d_umap = nullptr;          // caller's facets of all specimens, concatenated: 2 f + orientation flip
     std::vector<int64_t> ufoff;         // [n_spec + 1] offsets of each specimen's facets in d_umap
     double *d_scratch = nullptr;        // state read-back scratch, grown on demand
@@ -229,7 +230,7 @@ void free_model(ldpm_ctx *h)
                     h->dm.tet,
                     h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
-                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch};
+                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch, h->d_ticket};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_out16) cudaFreeHost(h->h_out16);
@@ -888,8 +889,10 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         (rc = dalloc(&dm.tet, (size_t)T)) || (rc = dalloc(&dm.row, (size_t)N + 1)) ||
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
-        (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())))
+        (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())) ||
+        (rc = dalloc(&h->d_ticket, 1)))
         return rc;
+    CU(cudaMemset(h->d_ticket, 0, sizeof(unsigned)));
     CU(cudaMemcpy(h->d_umap, umap.data(), umap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (H.any_fext) {
         if ((rc = dalloc(&dm.f_ext, 6 * (size_t)N))) return rc;
@@ -1442,7 +1445,7 @@ int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *his
 static int energy_of(ldpm_t h, int s, double out[4], double reaction[12])
 {
     const SpecHost &S = h->sp[s];
-    cudaError_t e = launch_energy(h->dm, S.p0, S.p0 + S.N, h->d_partial, h->d_out16, h->stream);
+    cudaError_t e = launch_energy(h->dm, S.p0, S.p0 + S.N, h->d_partial, h->d_ticket, h->d_out16, h->stream);
     if (e != cudaSuccess) return fail(LDPM_E_CUDA, "energy launch: %s", cudaGetErrorString(e));
     CU(cudaMemcpyAsync(h->h_out16, h->d_out16, 16 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));

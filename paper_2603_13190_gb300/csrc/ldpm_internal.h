@@ -137,9 +137,10 @@ cudaError_t launch_mirror(const DeviceModel &m, cudaStream_t s);
 template <class R>
 cudaError_t launch_gather(const DeviceModel &m, int mode, double *out6, cudaStream_t s);
 // Energy sums over particles [p0, p1): out16 = W_int, W_ext, W_kin, pad, reaction fixed(6),
-// reaction prescribed(6).  `partial` holds ceil((p1 - p0) / 256) * 16 doubles.
-cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, double *out16,
-                          cudaStream_t s);
+// reaction prescribed(6).  `partial` holds ceil((p1 - p0) / 256) * 16 doubles; `ticket` is a device
+// counter, 0 before the first launch, which each launch leaves at 0 again.
+cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, unsigned *ticket,
+                          double *out16, cudaStream_t s);
 // History of n facets in the caller's order (out5 [n][5]: t_N, tangential traction vector, e_max);
 // umap[k] = 2 f + s, f the internal facet, s = 1 where the caller's facet has the opposite orientation.
 template <class R>

@@ -684,10 +684,33 @@ __global__ void __launch_bounds__(256) perturb_kernel(DeviceModel m, const doubl
 }
 
 // Energy sums over particles [p0, p1) (per block, fixed order), then one block adds the partials.
-__global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, int32_t p1, double *partial)
+// Warp sum of 16 values per lane by halving exchanges: at each level a lane keeps half of its values
+// and adds its partner's copy of that half (8 + 4 + 2 + 1 + 1 additions).  Afterwards lanes 2i and
+// 2i + 1 both hold the warp sum of value i.  The order of the additions is fixed.
+__device__ __forceinline__ double warp_sum16(double (&v)[16], int lane)
 {
-    __shared__ double red[256][16];
-    const int tid = threadIdx.x;
+#pragma unroll
+    for (int h = 8, off = 16; h >= 1; h >>= 1, off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double keep = upper ? v[h + i] : v[i];
+            const double give = upper ? v[i] : v[h + i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, give, off);
+        }
+    }
+    return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+
+// Energy terms of particles [p0, p1): per block a fixed-order sum into partial[block][16]; the block
+// that finishes last (ticket from an atomic counter that wraps back to 0) sums the partials in block
+// order into out16.  No thread waits on another block.
+__global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, int32_t p1, double *partial,
+                                                     unsigned *ticket, double *out16)
+{
+    __shared__ double red[8][16];
+    __shared__ bool last;
+    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
     const int64_t p = (int64_t)p0 + (int64_t)blockIdx.x * 256 + tid;
     double acc[16];
 #pragma unroll
@@ -715,47 +738,32 @@ __global__ void __launch_bounds__(256) energy_kernel(DeviceModel m, int32_t p0, 
             else
                 v = m.bc_vel[6 * p + d] * ramp(t, S.inv_ramp);
             acc[2] += 0.5 * mass * v * v;
-            const int mask = (int)((bcbits >> (8 * d)) & 0xffu);
-            if (mask == 1) {
+            if (mk == 1) {
                 acc[4 + d] += -pd[d];
-            } else if (mask == 2) {
+            } else if (mk == 2) {
                 const double ra = ramp(t + 0.5 * dt, S.inv_ramp) - ramp(t - 0.5 * dt, S.inv_ramp);
                 acc[10 + d] += m.bc_vm[6 * p + d] * ra * S.inv_dt - pd[d];
             }
         }
     }
-#pragma unroll
-    for (int k = 0; k < 16; ++k) red[tid][k] = acc[k];
+    const double ws = warp_sum16(acc, lane);
+    if ((lane & 1) == 0) red[w][lane >> 1] = ws;
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (tid < w)
+    if (tid < 16) {
+        double b = 0.0;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) red[tid][k] += red[tid + w][k];
-        __syncthreads();
+        for (int k = 0; k < 8; ++k) b += red[k][tid];
+        partial[16 * (int64_t)blockIdx.x + tid] = b;
+        __threadfence();
     }
-    if (tid < 16) partial[16 * (int64_t)blockIdx.x + tid] = red[0][tid];
-}
-
-__global__ void __launch_bounds__(256) energy_final_kernel(const double *partial, int32_t nb, double *out16)
-{
-    __shared__ double red[256][16];
-    const int tid = threadIdx.x;
-    double acc[16];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc[k] = 0.0;
-    for (int b = tid; b < nb; b += 256)
-#pragma unroll
-        for (int k = 0; k < 16; ++k) acc[k] += partial[16 * (int64_t)b + k];
-#pragma unroll
-    for (int k = 0; k < 16; ++k) red[tid][k] = acc[k];
     __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-        if (tid < w)
-#pragma unroll
-            for (int k = 0; k < 16; ++k) red[tid][k] += red[tid + w][k];
-        __syncthreads();
+    if (tid == 0) last = atomicInc(ticket, gridDim.x - 1) == gridDim.x - 1;
+    __syncthreads();
+    if (last && tid < 16) {
+        double s = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) s += __ldcg(partial + 16 * (int64_t)k + tid);
+        out16[tid] = s;
     }
-    if (tid < 16) out16[tid] = red[0][tid];
 }
 
 // History <-> caller format (t_N, global tangential traction, e_max), in the internal facet order.
@@ -953,13 +961,12 @@ cudaError_t launch_perturb(const DeviceModel &m, const double *dq, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, double *out16,
-                          cudaStream_t s)
+cudaError_t launch_energy(const DeviceModel &m, int32_t p0, int32_t p1, double *partial, unsigned *ticket,
+                          double *out16, cudaStream_t s)
 {
     const int32_t nb = (p1 - p0 + 255) / 256;
     if (nb <= 0) return cudaMemsetAsync(out16, 0, 16 * sizeof(double), s);
-    energy_kernel<<<nb, 256, 0, s>>>(m, p0, p1, partial);
-    energy_final_kernel<<<1, 256, 0, s>>>(partial, nb, out16);
+    energy_kernel<<<nb, 256, 0, s>>>(m, p0, p1, partial, ticket, out16);
     return cudaGetLastError();
 }
 
