@@ -499,6 +499,7 @@ def run_adjoint(args, rank, world, local):
         store_all = {"skipped": "step inputs of all %d steps (%.0f GB) exceed 70 %% of free memory" % (K, need / 1e9)}
     fb64 = adjoint_facet_bytes(F, T, N, 8)
     value = job_value(world, F, K, dev_ms)
+    nseg = (K + C - 1) // C
     return {
         "metric": ADJ_METRIC, "value": value, "unit": "facet-updates/s", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": dev_ms / K, "higher_is_better": True, "scaling": "weak",
@@ -523,7 +524,10 @@ def run_adjoint(args, rank, world, local):
         "e2e": {"value": world * F * K / wall, "unit": "facet-updates/s", "h2d_bytes_per_step": seed.nbytes / K,
                 "d2h_bytes_per_step": (3 * F * 8 + 8) / K, "seconds": wall,
                 "what": "one ldpm_adjoint call: seed from host memory, gradients to host memory"},
-        "gpu_launches": 2 * K + 2 * K + K + 2 * (K // C + 1),
+        # forward sweep: facet, particle and objective kernels per step; recompute of every segment but
+        # the last: facet and particle kernels; reverse: reverse facet and particle kernels; one init,
+        # one fold per segment
+        "gpu_launches": 3 * K + 2 * (K - (K - (nseg - 1) * C)) + 2 * K + 1 + nseg,
         "clocks": sampler.summary() if sampler else None,
     }
 
