@@ -618,6 +618,44 @@ def run_reference(args, rank, world):
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def counters(args):
+    """Algorithmic bytes of each kernel of the workload: what the formulas above count per facet,
+    tetrahedron and particle, and the totals of one launch and one step, in both precisions."""
+    from paper_2603_13190_gb300 import workloads
+
+    if args.workload == "batched_unconfined_compression":
+        specs = workloads.batch_specimens(args.batch, seed=1)
+    else:
+        specs = [workloads.WORKLOADS[args.workload].specimen()]
+    N = sum(sp.n_particles for sp in specs)
+    T = sum(sp.n_tets for sp in specs)
+    F = sum(sp.n_facets for sp in specs)
+    out = {"workload": args.workload, "specimens": len(specs), "particles": N, "tets": T, "facets": F,
+           "per_unit": {
+               "facet_pass": {"per_facet": "geometry 4R + history read and written 8R",
+                              "per_tet": "16 B ids + 4 vertex shares of 6R",
+                              "per_particle": "gathered record, 84 B mixed / 120 B FP64"},
+               "particle_pass": {"per_tet": "4 slot ids (4 B) + 4 shares read (6R)",
+                                 "per_particle": "row 4 B, q/v 192 B, forces and energy sums 128 B, constants "
+                                                 "64 B, FP32 record written 84 B (mixed)"},
+               "reverse_facet_pass": {"per_facet": "geometry 4R, history 4R, carried adjoint 8R, gradient "
+                                                   "accumulators 8R",
+                                      "per_tet": "16 B ids + 4 vertex shares of 12R",
+                                      "per_particle": "forward record + a_f record, 120 B mixed / 168 B FP64"},
+               "reverse_particle_pass": {"per_tet": "4 slot ids + 4 shares read (12R)",
+                                         "per_particle": "row 4 B, Qbar/Ubar 192 B, seed 48 B, constants 64 B, "
+                                                         "a_f record written 36 B mixed / 48 B FP64"}},
+           "R": {"mixed": 4, "fp64": 8}}
+    for prec, r in (("mixed", 4), ("fp64", 8)):
+        fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(T, N, r)
+        afb, agb = adjoint_facet_bytes(F, T, N, r), adjoint_gather_bytes(T, N, r)
+        out[prec] = {"facet_pass_bytes": fb, "particle_pass_bytes": gb, "step_bytes": fb + gb,
+                     "reverse_facet_pass_bytes": afb, "reverse_particle_pass_bytes": agb,
+                     "adjoint_step_bytes": 2 * (fb + gb) + afb + agb,
+                     "step_bytes_per_facet": (fb + gb) / F}
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -629,11 +667,17 @@ def main():
                              "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--counters", action="store_true",
+                    help="print the algorithmic bytes of each kernel for the workload (per-unit figures and "
+                         "totals per launch and per step) and exit; no GPU is used")
     ap.add_argument("--ncu-case", choices=("mixed", "fp64", "adjoint"), default=None,
                     help="profiling target: create the workload (dt = 2e-7 s, no estimate), run 4 steps "
                          "with plain launches (adjoint: one 8-step ldpm_adjoint, checkpoints every 4 "
                          "steps, on the adjoint workload in mixed precision) and exit; nothing is timed")
     args = ap.parse_args()
+    if args.counters:
+        print(json.dumps(counters(args)), flush=True)
+        return
     if args.ncu_case:
         from paper_2603_13190_gb300 import ldpm
 
