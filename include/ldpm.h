@@ -39,7 +39,7 @@ extern "C" {
 #define LDPM_E_CUDA (-3)          /* a CUDA call failed (message names it) */
 #define LDPM_E_OOM (-4)           /* device or host allocation failed */
 #define LDPM_E_UNSTABLE (-5)      /* a velocity or displacement became NaN/Inf (step too large?) */
-#define LDPM_E_TIMEOUT (-6)       /* a bounded device-side wait expired */
+#define LDPM_E_TIMEOUT (-6)       /* reserved for a bounded device-side wait; no kernel waits today */
 #define LDPM_E_UNSUPPORTED (-7)   /* a parameter combination the library does not implement */
 
 typedef struct ldpm_ctx *ldpm_t; /* opaque handle, owned by the library */
