@@ -1202,23 +1202,40 @@ int adjoint_run(ldpm_ctx *h, int64_t K, int64_t C, const double *seed, double *J
         return LDPM_OK;
     };
     const bool grads = gE0 || galpha || gsigma;
-    // keep the inputs of a step (the particle records it reads and the history before it) in slot i
-    auto keep_inputs = [&](int64_t i) -> int {
-        char *sl = snap + snap_stride * i;
-        CU(cudaMemcpyAsync(sl, mixed ? (const void *)h->dm.pm32 : (const void *)h->dm.pstate, rec,
-                           cudaMemcpyDeviceToDevice, h->stream));
-        CU(cudaMemcpyAsync(sl + align256(rec), h->dm.hist, hb, cudaMemcpyDeviceToDevice, h->stream));
-        return LDPM_OK;
+    // n steps from the model's state keeping each step's inputs in slot i: the particle records it
+    // reads are copied there, and its history is read from the slot itself.  Slot 0 receives the
+    // model's history; step i writes its new history into slot i + 1 (the last step into the model's
+    // own buffer), so the history is never copied per step.
+    auto run_kept = [&](int64_t n, bool objective) -> int {
+        void *own = h->dm.hist;
+        CU(cudaMemcpyAsync(snap + align256(rec), own, hb, cudaMemcpyDeviceToDevice, h->stream));
+        int r = LDPM_OK;
+        for (int64_t i = 0; i < n && r == LDPM_OK; ++i) {
+            char *sl = snap + snap_stride * i;
+            cudaError_t e = cudaMemcpyAsync(sl, mixed ? (const void *)h->dm.pm32 : (const void *)h->dm.pstate, rec,
+                                            cudaMemcpyDeviceToDevice, h->stream);
+            if (e != cudaSuccess) {
+                r = fail(LDPM_E_CUDA, "adjoint: step input copy: %s", cudaGetErrorString(e));
+                break;
+            }
+            h->dm.hist = sl + align256(rec);
+            h->dm.hist_out = i + 1 < n ? (void *)(snap + snap_stride * (i + 1) + align256(rec)) : own;
+            r = fwd(objective);
+        }
+        h->dm.hist = own;
+        h->dm.hist_out = nullptr;
+        return r;
     };
     // forward sweep: checkpoint at the start of every segment, and the final state.  The last segment
     // is the first one reversed, so its step inputs are kept now instead of being recomputed.
     for (int64_t sg = 0; sg < nseg; ++sg) {
         if ((rc = state_copy(h, ckpt + stride * sg, true))) return rc;
-        const bool last = grads && sg == nseg - 1;
         const int64_t n = std::min(C, K - sg * C);
-        for (int64_t i = 0; i < n; ++i) {
-            if (last && (rc = keep_inputs(i))) return rc;
-            if ((rc = fwd(true))) return rc;
+        if (grads && sg == nseg - 1) {
+            if ((rc = run_kept(n, true))) return rc;
+        } else {
+            for (int64_t i = 0; i < n; ++i)
+                if ((rc = fwd(true))) return rc;
         }
     }
     if ((rc = state_copy(h, ckpt + stride * nseg, true))) return rc;
@@ -1230,8 +1247,7 @@ int adjoint_run(ldpm_ctx *h, int64_t K, int64_t C, const double *seed, double *J
             const int64_t n = std::min(C, K - sg * C);
             if (sg < nseg - 1) {  // recompute the segment from its checkpoint, keeping each step's inputs
                 if ((rc = state_copy(h, ckpt + stride * sg, false))) return rc;
-                for (int64_t i = 0; i < n; ++i)
-                    if ((rc = keep_inputs(i)) || (rc = fwd(false))) return rc;
+                if ((rc = run_kept(n, false))) return rc;
             }
             for (int64_t i = n - 1; i >= 0; --i) {
                 char *sl = snap + snap_stride * i;

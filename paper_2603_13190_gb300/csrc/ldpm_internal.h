@@ -87,6 +87,7 @@ struct DeviceModel {
     double *bc_vm = nullptr;        // [N][6] prescribed velocity times the DOF's mass
     int4 *tet = nullptr;
     void *geo = nullptr, *hist = nullptr, *fout = nullptr, *tvc = nullptr, *ent = nullptr;
+    void *hist_out = nullptr;  // where a stepping facet pass writes the new history (null: hist, in place)
     void *pf = nullptr;             // per-facet E0, alpha, sigma_t (R4 [12T]) or null
     int32_t *row = nullptr;
     int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)

@@ -173,7 +173,7 @@ __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, in
 {
     using T4 = R4<R>;
     constexpr int E = 16 / (int)sizeof(R);
-    T4 *__restrict__ hist = static_cast<T4 *>(m.hist);
+    T4 *__restrict__ hout = static_cast<T4 *>(m.hist_out ? m.hist_out : m.hist);  // the new history
     T4 *__restrict__ fout = static_cast<T4 *>(m.fout);
     const LawConst<R> *__restrict__ lawc = static_cast<const LawConst<R> *>(m.law);
     (void)pp;
@@ -246,7 +246,7 @@ __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, in
             hn.y = tM;
             hn.z = tL;
             hn.w = emax;
-            hist[f] = hn;
+            hout[f] = hn;
         }
     }
     const R Ar = g.w;
