@@ -402,9 +402,10 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     }
     for (int32_t r = 0; r < S.T_pad / kTile; ++r) H.tile_spec[S.t0 / kTile + r] = s;
     // ---- facets: slot = 2 * edge + k within the tetrahedron; the first of an edge's two facets in the
-    // caller's order takes the lower slot.  Three passes: the facet's tetrahedron and edge (parallel),
-    // the slots (sequential, in the caller's order), the geometry (parallel).  Each check reports the
-    // first failing facet in the caller's order, as one sequential loop would.
+    // caller's order takes the lower slot.  Three passes on host threads: the facet's tetrahedron and
+    // edge; the slots (each thread owns a range of tetrahedra and scans the facets in the caller's
+    // order); the geometry.  Each check reports the first failing facet in the caller's order, as one
+    // sequential loop would.
     S.fmap.assign(F, -1);
     S.fswap.assign(F, 0);
     std::vector<int32_t> rank(F);  // Morton rank of the facet's tetrahedron
