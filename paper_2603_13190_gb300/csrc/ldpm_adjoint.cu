@@ -333,6 +333,11 @@ constexpr int kATets = 8;
 constexpr int kARow = 16;  // state row: dx(3) du(3) dv(3) theta(3) omega(3) pad
 constexpr int kAFr = 8;    // a_f row: da_u(3) a_theta(3) pad(2)
 constexpr int kACon = 24;  // facet contributions: vertex a: q(6) u(6), vertex b: q(6) u(6)
+// The contributions are stored vertex-major, as in the forward warp kernel: plane 2 s + h (s = 0..5
+// the facet's position in its vertex's fixed summation order, h = 0 for the q half, 1 for the u half)
+// holds 6 values per vertex of the tile, so the vertex sums of task t = 12 j + 3 v + q read words
+// 2t, 2t + 1 of each plane (contiguous, no bank conflicts).
+constexpr int kAPlane = 6 * 4 * kATets + 2;
 
 // Mixed mode: 8 resident blocks per SM.  The register cap (80 per thread) costs 24 bytes of spills
 // and doubles the occupancy of the uncapped build; measured 10 % faster on GB300.  The FP64 build
@@ -345,7 +350,7 @@ __global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_f
     constexpr int TETS = kATets;
     __shared__ alignas(16) R sv[TETS * 4][kARow + 2];
     __shared__ alignas(16) R sa[TETS * 4][kAFr];
-    __shared__ R scon[12 * TETS][kACon + 1];
+    __shared__ alignas(16) R spl[12 * kAPlane];
     __shared__ R sgrad[TETS][4][3];
     __shared__ R saeV[12 * TETS];
     __shared__ R seV[TETS];
@@ -602,31 +607,42 @@ __global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_f
         cs[22] = Mbd.y;
         cs[23] = Mbd.z;
     }
+    {
+        // edge e = slot / 2 joins local vertices va < vb; it is the ka-th edge of va and the kb-th of
+        // vb (ascending), so this facet is entry 2 ka + slot % 2 of va's order, 2 kb + slot % 2 of vb's
+        using V2 = typename VecT<R>::v2;
+        const int e = slot >> 1, sw = slot & 1;
+        const int va = (0x211000 >> (4 * e)) & 0xF, vb = (0x332321 >> (4 * e)) & 0xF;
+        const int ka = (0x221210 >> (4 * e)) & 0xF, kb = (0x211000 >> (4 * e)) & 0xF;
 #pragma unroll
-    for (int k = 0; k < kACon; ++k) scon[tid][k] = cs[k];
+        for (int hf = 0; hf < 2; ++hf) {
+            R *da = spl + (2 * (2 * ka + sw) + hf) * kAPlane + 6 * (4 * j + va);
+            R *db = spl + (2 * (2 * kb + sw) + hf) * kAPlane + 6 * (4 * j + vb);
+#pragma unroll
+            for (int c = 0; c < 6; c += 2) {
+                *reinterpret_cast<V2 *>(da + c) = V2{cs[6 * hf + c], cs[6 * hf + c + 1]};
+                *reinterpret_cast<V2 *>(db + c) = V2{cs[12 + 6 * hf + c], cs[12 + 6 * hf + c + 1]};
+            }
+        }
+    }
     saeV[tid] = aeV;
     __syncthreads();
 
     // ---- phase C: thread `slot` of tetrahedron j: vertex v = slot / 3, components 2 q, 2 q + 1 of
     // both halves (q = slot % 3), over the vertex's 3 edges (ascending), each edge's two facets
     if (live) {
+        using V2 = typename VecT<R>::v2;
         const int v = slot / 3;
         const int q = slot - 3 * v;
-        const int edges = (int)((0x542531430210ull >> (12 * v)) & 0xFFF);
-        const int sides = (0xEC8 >> (3 * v)) & 0x7;
         R s[4] = {R(0), R(0), R(0), R(0)};
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const int e2 = (edges >> (4 * k)) & 0xF;
-            const int col = (((sides >> k) & 1) ? 12 : 0) + 2 * q;
-#pragma unroll
-            for (int w = 0; w < 2; ++w) {
-                const R *row = scon[12 * j + 2 * e2 + w];
-                s[0] += row[col];
-                s[1] += row[col + 1];
-                s[2] += row[col + 6];
-                s[3] += row[col + 7];
-            }
+        for (int sp = 0; sp < 6; ++sp) {
+            const V2 xq = *reinterpret_cast<const V2 *>(spl + (2 * sp) * kAPlane + 2 * tid);
+            const V2 xu = *reinterpret_cast<const V2 *>(spl + (2 * sp + 1) * kAPlane + 2 * tid);
+            s[0] += xq.x;
+            s[1] += xq.y;
+            s[2] += xu.x;
+            s[3] += xu.y;
         }
         if (q < 2) {  // displacement components 0..2 also receive grad(e_V) times the summed a_eV
             R aT = R(0);

@@ -354,22 +354,29 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 // alone (lane = vertex in phase A, three facets per lane in phase B, three vertex sums per lane in
 // phase C), synchronising only within the warp, so each warp's record gathers are in flight
 // independently of the other warps.  Same arithmetic and summation order as facet_kernel<.., 8, ..>.
+// The facets' contributions are stored vertex-major: plane s (0..5) holds, for every vertex of the
+// tile, the contribution of the s-th facet in that vertex's fixed summation order (its 3 edges
+// ascending, each edge's two facets in slot order), 6 values per vertex.  The vertex sum of
+// components 2q, 2q+1 of vertex v of tetrahedron j (task t = 12 j + 3 v + q) then reads word 2t of
+// each plane: contiguous for the lanes, free of bank conflicts.  Planes are kPlane words apart (192
+// plus 2, so that the facets' stores into different planes fall on different banks).
 constexpr int kTileTets = 8;
+constexpr int kPlane = 6 * 4 * kTileTets + 2;
 template <class R, int MODE, int WPB, bool PF>
 __global__ void __launch_bounds__(32 * WPB) facet_warp_kernel(DeviceModel m, const void *__restrict__ vsrc)
 {
     using T4 = R4<R>;
-    constexpr int E = 16 / (int)sizeof(R);
+    using V2 = typename VecT<R>::v2;
     constexpr int TETS = kTileTets;
     __shared__ alignas(16) R sv_[WPB][TETS * 4][Stride<R>::row];
-    __shared__ alignas(16) R scon_[WPB][12 * TETS][Stride<R>::con];
+    __shared__ alignas(16) R spl_[WPB][6 * kPlane];
     __shared__ R seV_[WPB][TETS];
     __shared__ int sok_[WPB][TETS];
     const T4 *__restrict__ geo = static_cast<const T4 *>(m.geo);
     const T4 *__restrict__ hist = static_cast<const T4 *>(m.hist);
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     R(*sv)[Stride<R>::row] = sv_[w];
-    R(*scon)[Stride<R>::con] = scon_[w];
+    R *spl = spl_[w];
     R *seV = seV_[w];
     int *sok = sok_[w];
     const int64_t tet0 = ((int64_t)blockIdx.x * WPB + w) * TETS;
@@ -397,19 +404,42 @@ __global__ void __launch_bounds__(32 * WPB) facet_warp_kernel(DeviceModel m, con
         const int fi = lane + 32 * i;
         const int j = fi / 12;
         const bool live = tet0 + j < m.T && sok[j];
+        const int slot = fi - 12 * j;
         R cs[12];
-        facet_one<R, MODE, PF>(m, tet0, j, fi - 12 * j, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs);
+        facet_one<R, MODE, PF>(m, tet0, j, slot, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs);
+        if (MODE != FACET_METRIC) {
+            // edge e = slot / 2 joins local vertices va < vb; it is the ka-th edge of va and the kb-th
+            // of vb (ascending), so this facet is entry 2 ka + slot % 2 of va's order, 2 kb + slot % 2 of vb's
+            const int e = slot >> 1, sw = slot & 1;
+            const int va = (0x211000 >> (4 * e)) & 0xF, vb = (0x332321 >> (4 * e)) & 0xF;
+            const int ka = (0x221210 >> (4 * e)) & 0xF, kb = (0x211000 >> (4 * e)) & 0xF;
+            R *da = spl + (2 * ka + sw) * kPlane + 6 * (4 * j + va);
+            R *db = spl + (2 * kb + sw) * kPlane + 6 * (4 * j + vb);
 #pragma unroll
-        for (int k = 0; k < kCon; k += E) VecT<R>::put(&scon[fi][k], &cs[k]);
+            for (int c = 0; c < 6; c += 2) {
+                *reinterpret_cast<V2 *>(da + c) = V2{cs[c], cs[c + 1]};
+                *reinterpret_cast<V2 *>(db + c) = V2{cs[6 + c], cs[6 + c + 1]};
+            }
+        }
     }
     __syncwarp();
-    // ---- phase C
+    // ---- phase C: task t = 12 j + 3 v + q sums components 2q, 2q+1 of vertex v over the 6 planes
     if (MODE != FACET_METRIC) {
+        R *__restrict__ tvc = static_cast<R *>(m.tvc);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             const int t = lane + 32 * i;
             const int j = t / 12;
-            if (tet0 + j < m.T && sok[j]) vertex_sum<R>(m, tet0, j, t - 12 * j, scon);
+            if (tet0 + j < m.T && sok[j]) {
+                R s0 = R(0), s1 = R(0);
+#pragma unroll
+                for (int sp = 0; sp < 6; ++sp) {
+                    const V2 x = *reinterpret_cast<const V2 *>(spl + sp * kPlane + 2 * t);
+                    s0 += x.x;
+                    s1 += x.y;
+                }
+                *reinterpret_cast<V2 *>(tvc + tet0 * 24 + 2 * t) = V2{s0, s1};
+            }
         }
     }
 }
