@@ -83,3 +83,29 @@ def test_batch_rejects_single_specimen_calls(trio):
         ldpm.ldpm_energy(b.h)
     with pytest.raises(ldpm.LdpmError):
         ldpm.ldpm_set_bc(b.h, bcs[0].mask, bcs[0].vel, 0.0)
+
+
+def test_full_size_batch_one_step_against_oracle():
+    """The benchmark's batch at full size (64 cubes, 97.7M facets) in the launch shape the autotuner
+    picks for it, as the benchmark runs it: after a few steps, one more step of three sampled cubes
+    against the FP64 oracle started from the batch's own state of those cubes."""
+    specs = workloads.batch_specimens(64, seed=1)
+    bcs = [workloads.unconfined_compression_bc(sp) for sp in specs]
+    mats = [dict(MAT) for _ in specs]
+    b = ldpm.Batch(specs, mats, "mixed", bcs=bcs, autotune=True)
+    assert len(b) == 64 and sum(sp.n_facets for sp in specs) > 9e7
+    b.step(20)
+    picks = (0, 31, 63)
+    before = {i: b.get_state(i) for i in picks}
+    b.step(1)
+    for i in picks:
+        q, v, h5, st = before[i]
+        dt = b.info(i)[1]
+        o = oracle.Oracle(specs[i], mats[i], dt, bcs[i])
+        o.set_state(q, v, h5, st)
+        o.step(1)
+        qo, vo, _, _ = o.get_state()
+        qg, vg, _, stg = b.get_state(i)
+        assert stg == st + 1
+        assert nrel(qg, qo) <= 2e-5 and nrel(vg, vo) <= 2e-5, (i, nrel(qg, qo), nrel(vg, vo))
+    b.close()
