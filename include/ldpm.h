@@ -144,7 +144,9 @@ int ldpm_sync(ldpm_t h);
 /* Copy the state out (synchronises).  q, v: [N][6]; hist5: [F][5] per facet t_N, the tangential
  * traction t_M m + t_L l as a global 3-vector, e_max (the traction acting on facet_pi[k]); step: the
  * step counter.  Any pointer may be NULL.  Returns UNSTABLE after a non-finite state (data still
- * copied). */
+ * copied).  The history is put in the caller's facet order on the device and copied straight into
+ * hist5; the first call allocates a device scratch buffer of 12 N + 5 F doubles that the handle keeps
+ * until ldpm_destroy (OOM if it cannot). */
 int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step);
 
 /* Replace the state (synchronises).  Same layouts as ldpm_get_state; hist5 may be NULL (zero
