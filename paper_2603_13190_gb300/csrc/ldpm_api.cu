@@ -89,12 +89,17 @@ uint32_t morton3(const double *p, const double *lo, const double *span)
 // fn(lo, hi) over contiguous chunks of [0, n) on up to 16 host threads (one thread below 65536
 // items); returns the smallest of the chunks' results.  The checks below return the first failing
 // item of their chunk (or a sentinel), so the result is the item a sequential loop would report.
+// Host threads parallel_min uses for n items: up to 16, one below 65536 items.
+unsigned host_threads(int64_t n)
+{
+    const unsigned hw = std::thread::hardware_concurrency();
+    return n < 65536 ? 1u : std::max(1u, std::min(hw, 16u));
+}
+
 template <class Fn>
 int64_t parallel_min(int64_t n, Fn &&fn)
 {
-    unsigned nt = std::thread::hardware_concurrency();
-    nt = std::max(1u, std::min(nt, 16u));
-    if (n < 65536) nt = 1;
+    const unsigned nt = host_threads(n);
     if (nt == 1) return fn((int64_t)0, n);
     std::vector<int64_t> res(nt, INT64_MAX);
     std::vector<std::thread> th;
@@ -292,12 +297,12 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     const ldpm_material &mat = S.mat;
     // ---- tetrahedra
     std::vector<double> tvol(T);
-    for (int32_t t = 0; t < T; ++t) {
+    auto tet_check = [&](int32_t t) -> int {  // 0 ok, 1 index out of range, 2 repeated, 3 volume
         const int32_t *v = g.tet + 4 * (size_t)t;
         for (int i = 0; i < 4; ++i) {
-            if (v[i] < 0 || v[i] >= N) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: particle index out of range", t);
+            if (v[i] < 0 || v[i] >= N) return 1;
             for (int k = 0; k < i; ++k)
-                if (v[k] == v[i]) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: repeated particle", t);
+                if (v[k] == v[i]) return 2;
         }
         double d[3][3];
         for (int i = 0; i < 3; ++i)
@@ -305,9 +310,21 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
         const double det = d[0][0] * (d[1][1] * d[2][2] - d[1][2] * d[2][1]) -
                            d[0][1] * (d[1][0] * d[2][2] - d[1][2] * d[2][0]) +
                            d[0][2] * (d[1][0] * d[2][1] - d[1][1] * d[2][0]);
-        if (!(std::fabs(det) > 0) || !std::isfinite(det))
-            return fail(LDPM_E_BAD_GEOMETRY, "tet %d: zero or non-finite volume", t);
+        if (!(std::fabs(det) > 0) || !std::isfinite(det)) return 3;
         tvol[t] = std::fabs(det) / 6.0;
+        return 0;
+    };
+    const int64_t bad_t = parallel_min(T, [&](int64_t t0, int64_t t1) -> int64_t {
+        for (int64_t t = t0; t < t1; ++t)
+            if (tet_check((int32_t)t)) return t;
+        return (int64_t)T;
+    });
+    if (bad_t < T) {
+        const int32_t t = (int32_t)bad_t;
+        const int kind = tet_check(t);
+        if (kind == 1) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: particle index out of range", t);
+        if (kind == 2) return fail(LDPM_E_BAD_GEOMETRY, "tet %d: repeated particle", t);
+        return fail(LDPM_E_BAD_GEOMETRY, "tet %d: zero or non-finite volume", t);
     }
     for (int32_t i = 0; i < 3 * N; ++i)
         if (!std::isfinite(g.x[i])) return fail(LDPM_E_BAD_GEOMETRY, "particle coordinate is not finite");
@@ -410,6 +427,10 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     S.fswap.assign(F, 0);
     std::vector<int32_t> rank(F);  // Morton rank of the facet's tetrahedron
     std::vector<uint8_t> lalb(F);  // local vertex indices la | lb << 2, edge << 4
+    // the slot pass below runs parallel_min over the T ranks: owner[k] is the thread whose range
+    // holds the facet's rank, so each thread scans one byte per facet
+    const int64_t rank_chunk = ((int64_t)T + host_threads(T) - 1) / host_threads(T);
+    std::vector<uint8_t> owner(F);
     int kind1 = 0;
     const int64_t bad1 = parallel_min(F, [&](int64_t lo, int64_t hi) -> int64_t {
         for (int64_t k = lo; k < hi; ++k) {
@@ -423,6 +444,7 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
             }
             if (la < 0 || lb < 0 || la == lb) return k;
             rank[k] = inv_t[t];
+            owner[k] = (uint8_t)(inv_t[t] / rank_chunk);
             lalb[k] = (uint8_t)(la | (lb << 2) | (edge_of(la, lb) << 4));
         }
         return (int64_t)F;
@@ -435,10 +457,12 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     // ranks and scans all facets in the caller's order, taking those of its tetrahedra.
     std::vector<uint8_t> used((size_t)T * 12, 0);
     const int64_t bad2 = parallel_min(T, [&](int64_t r0, int64_t r1) -> int64_t {
+        const uint8_t me = (uint8_t)(r0 / rank_chunk);
+        const bool one_chunk = r1 - r0 <= rank_chunk;  // false only when run on a single thread
         int64_t first = bad1;
         for (int64_t k = 0; k < bad1; ++k) {
+            if (one_chunk ? owner[k] != me : (rank[k] < r0 || rank[k] >= r1)) continue;
             const int64_t rt = rank[k];
-            if (rt < r0 || rt >= r1) continue;
             int slot = 2 * (lalb[k] >> 4);
             if (used[(size_t)rt * 12 + slot]) ++slot;
             if (used[(size_t)rt * 12 + slot]) {
@@ -507,10 +531,14 @@ int prepare_specimen(int s, const ldpm_geometry &g, const ldpm_options &o, SpecH
     if (kind1 == 1) return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: tetrahedron index out of range", (long long)bad1);
     if (kind1 == 2)
         return fail(LDPM_E_BAD_GEOMETRY, "facet %lld: I and J must be two vertices of its tetrahedron", (long long)bad1);
-    for (int32_t r = 0; r < T; ++r)
-        for (int sl = 0; sl < 12; ++sl)
-            if (!used[(size_t)r * 12 + sl])
-                return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: edge without its two facets", perm_t[r]);
+    const int64_t bad_r = parallel_min(T, [&](int64_t r0, int64_t r1) -> int64_t {
+        for (int64_t r = r0; r < r1; ++r)
+            for (int sl = 0; sl < 12; ++sl)
+                if (!used[(size_t)r * 12 + sl]) return r;
+        return (int64_t)T;
+    });
+    if (bad_r < T)
+        return fail(LDPM_E_BAD_GEOMETRY, "tetrahedron %d: edge without its two facets", perm_t[bad_r]);
     return LDPM_OK;
 }
 
@@ -845,7 +873,11 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     umap.resize((size_t)h->ufoff[n]);
     for (int s = 0; s < n; ++s) {
         const SpecHost &S = h->sp[s];
-        for (int32_t k = 0; k < S.F; ++k) umap[(size_t)h->ufoff[s] + k] = (int32_t)(2 * S.fmap[k] + S.fswap[k]);
+        int32_t *dst = umap.data() + h->ufoff[s];
+        parallel_min(S.F, [&](int64_t k0, int64_t k1) -> int64_t {
+            for (int64_t k = k0; k < k1; ++k) dst[k] = (int32_t)(2 * S.fmap[k] + S.fswap[k]);
+            return 0;
+        });
     }
     // ---- device
     int dev = o0.device;
