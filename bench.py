@@ -64,20 +64,37 @@ def measured_peaks():
     return 6800.0, "fallback (6.8 TB/s)"
 
 
-def recorded_traffic(kernel: str, workload: str, prec: str):
-    """DRAM bytes per launch from a committed ncu summary, valid only for the kernel source it was
-    taken from (null otherwise)."""
+def recorded_traffic(kernel: str, workload: str, prec: str, field: str = "bytes_per_launch"):
+    """DRAM bytes (or another recorded count) per launch from a committed ncu summary, valid only for
+    the kernel source it was taken from (null otherwise)."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     try:
         d = json.load(open(p))
         e = d.get("%s/%s/%s" % (kernel, workload, prec))
-        if e and e.get("kernel_src_hash") == kernel_src_hash():
-            return float(e["bytes_per_launch"])
+        if e and e.get("kernel_src_hash") == kernel_src_hash() and field in e:
+            return float(e[field])
     except Exception:
         return None
     return None
+
+
+# FP64 FMA peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA per cycle x 2 flops x
+# 2.07 GHz (the rate ncu reports as sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_alu_roofline(workload: str, facet_ms: float):
+    """The FP64 facet pass against the FP64 pipe: FP64 flops of one launch (dadd + dmul + 2 dfma,
+    counted by ncu on the same kernel source) over the live launch time."""
+    fl = recorded_traffic("facet_kernel", workload, "fp64", "fp64_flops_per_launch")
+    if fl is None or not facet_ms:
+        return None
+    achieved = fl / (facet_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_launch": fl,
+            "peak_source": "derived: 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz"}
 
 
 class ClockSampler:
@@ -224,6 +241,7 @@ def run_ours(args, rank, world, local):
     for prec, steps in (("mixed", args.steps), ("fp64", max(3, args.steps // 4))):
         model = ldpm.Model(spec, wl.material, precision=prec, dt=dt0 or 0.0, bc=bc, stream=stream, device=local)
         dt0 = dt0 or model.dt
+        model.step(args.preroll)
         barrier(world)
         torch.cuda.synchronize()
         ms, _ = time_steps(model, ldpm, torch, stream, flush, steps, args.warmup, profile=False)
@@ -293,6 +311,8 @@ def run_ours(args, rank, world, local):
         "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
                    "particles": N, "tets": T, "facets": F, "precision": "mixed: FP32 facet pass, FP64 particle state",
                    "dt_s": dt0, "l2": "flushed (512 MB write) before every timed step, outside the timed interval",
+                   "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
+                       args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll, args.warmup),
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": wl.seed},
         "roofline": mx["roofline"],
         "gather_roofline": mx["gather_roofline"],
@@ -304,7 +324,8 @@ def run_ours(args, rank, world, local):
                  "step_roofline": out["fp64"]["step_roofline"],
                  "kernel_ms": {"kick": out["fp64"]["kick_ms"], "facet": out["fp64"]["facet_ms"],
                                "gather": out["fp64"]["gather_ms"]},
-                 "steady_state": out["fp64"]["steady_state"]},
+                 "steady_state": out["fp64"]["steady_state"],
+                 "alu_roofline": fp64_alu_roofline(args.workload, out["fp64"]["facet_ms"])},
         "mixed_over_fp64": mx["value"] / out["fp64"]["value"],
         "e2e": {"value": world * F * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": geo_bytes / K,
                 "d2h_bytes_per_step": d2h / K, "seconds": e2e_s,
@@ -344,6 +365,7 @@ def run_batch(args, rank, world, local):
         sampler.__enter__()
     barrier(world)
     torch.cuda.synchronize()
+    b.step(args.preroll)
     ms, _ = time_steps(b, ldpm, torch, stream, flush, args.steps, args.warmup, profile=False)
     torch.cuda.synchronize()
     barrier(world)
@@ -360,6 +382,7 @@ def run_batch(args, rank, world, local):
     b.close()
     # all-FP64 single-specimen path, same GPU: the batch's first specimen
     single = ldpm.Model(specs[0], mats[0], precision="fp64", bc=bcs[0], stream=stream, device=local)
+    single.step(args.preroll)
     ms64, _ = time_steps(single, ldpm, torch, stream, flush, max(3, args.steps // 4), args.warmup, profile=False)
     fp64_single = specs[0].n_facets * len(ms64) / (sum(ms64) * 1e-3)
     single.close()
@@ -375,6 +398,8 @@ def run_batch(args, rank, world, local):
                    "precision": "mixed: FP32 facet pass, FP64 particle state",
                    "launch_shape": {"tets_per_block": shape[0], "lanes_per_particle": shape[1], "by": "autotuner"},
                    "l2": "flushed (512 MB write) before every timed step, outside the timed interval",
+                   "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
+                       args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll, args.warmup),
                    "generation_s": round(gen_s, 1), "create_s": round(create_s, 1)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": None, "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
@@ -590,6 +615,7 @@ def run_reference(args, rank, world):
         seed = np.zeros((spec.n_particles, 6))
         seed[spec.face_nodes(2, 1), 2] = 1.0
         d = np.random.default_rng(0).standard_normal((8, spec.n_facets))
+    o.step(args.preroll)
     for _ in range(args.warmup):
         o.step(1)
     t = []
@@ -612,7 +638,10 @@ def run_reference(args, rank, world):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
                        "particles": spec.n_particles, "tets": spec.n_tets, "facets": spec.n_facets,
-                       "precision": "FP64 oracle", "dt_s": dt, "seed": wl.seed},
+                       "precision": "FP64 oracle", "dt_s": dt, "seed": wl.seed,
+                       "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
+                           args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll,
+                           args.warmup)},
             "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1,
                              "sample": what % (args.steps, args.warmup)},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -667,13 +696,18 @@ def main():
                              "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--preroll", type=int, default=200,
+                    help="untimed steps of the loading history before the warm-up: the timed window then sees "
+                         "every facet strained (the loading wave crosses a 50 mm cube in about 60 steps; "
+                         "before that, facets at zero strain take the law's cheap path)")
     ap.add_argument("--counters", action="store_true",
                     help="print the algorithmic bytes of each kernel for the workload (per-unit figures and "
                          "totals per launch and per step) and exit; no GPU is used")
     ap.add_argument("--ncu-case", choices=("mixed", "fp64", "adjoint"), default=None,
-                    help="profiling target: create the workload (dt = 2e-7 s, no estimate), run 4 steps "
-                         "with plain launches (adjoint: one 8-step ldpm_adjoint, checkpoints every 4 "
-                         "steps, on the adjoint workload in mixed precision) and exit; nothing is timed")
+                    help="profiling target: create the workload (dt = 2e-7 s, no estimate), run the pre-roll, "
+                         "then between profiler start and stop 4 steps with plain launches (adjoint: one "
+                         "8-step ldpm_adjoint, checkpoints every 4 steps, on the adjoint workload in mixed "
+                         "precision) and exit; nothing is timed")
     args = ap.parse_args()
     if args.counters:
         print(json.dumps(counters(args)), flush=True)
@@ -681,17 +715,27 @@ def main():
     if args.ncu_case:
         from paper_2603_13190_gb300 import ldpm
 
+        import torch
+
+        # the captured launches come after the pre-roll: run ncu with --profile-from-start off
         if args.ncu_case == "adjoint":
             wl, spec, bc = make_inputs("adjoint_uniaxial_tension")
             m = ldpm.Model(spec, wl.material, precision="mixed", dt=2e-7, bc=bc, graph_chunk=-1)
+            m.step(args.preroll)
+            m.sync()
             seed = np.zeros((spec.n_particles, 6))
             seed[spec.face_nodes(2, 1), 2] = 1.0
+            torch.cuda.profiler.start()
             m.adjoint(8, seed, 4)
         else:
             wl, spec, bc = make_inputs(args.workload)
             m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=2e-7, bc=bc, graph_chunk=-1)
+            m.step(args.preroll)
+            m.sync()
+            torch.cuda.profiler.start()
             m.step(4)
         m.sync()
+        torch.cuda.profiler.stop()
         m.close()
         print("ncu case done: F=%d" % spec.n_facets)
         return
