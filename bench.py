@@ -630,8 +630,9 @@ def run_reference(args, rank, world):
             t.append(time.perf_counter() - t0)
     tot = sum(t)
     val = spec.n_facets * args.steps / tot
-    what = ("%d steps each carrying 8 directional derivatives (forward mode), after %d warm-up steps, single thread"
-            if adjoint else "%d full explicit steps after %d warm-up steps, single thread")
+    what = ("%%d steps each carrying 8 directional derivatives (forward mode), after %d pre-roll and %%d warm-up "
+            "steps, single thread" if adjoint else
+            "%%d full explicit steps after %d pre-roll and %%d warm-up steps, single thread") % args.preroll
     return {"impl": "reference", "metric": ADJ_METRIC if adjoint else METRIC, "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
