@@ -197,6 +197,29 @@ def test_friction_cap_and_initial_slope_mu0():
     assert abs(c2 - (ss + mu0 * sN0 * (1 - math.exp(tN2 / sN0)))) < 1e-9 * c2
 
 
+def test_friction_cap_slope_runs_from_mu0_to_mu_inf():
+    """App. A.3: the friction cap sigma_bs(t_N) rises with slope mu_0 at t_N -> 0 and tends to slope
+    mu_inf under deep compression.  A material with mu_inf > 0 (the workloads use 0) and a compressive
+    yield stress far above the tested range, so t_N = E0 e_N stays elastic down to -12 sigma_N0.  The
+    slopes are finite differences of saturated plateaus; no formula of the cap is used."""
+    mat = dict(MAT, mu_inf=0.05, sigma_c0=1e6)
+    E0, a, sN0 = mat["E0"], mat["alpha"], mat["sigma_N0"]
+
+    def plateau(tN):
+        eN = tN / E0
+        cap = mat["r_st"] * mat["sigma_t"] + mat["mu0"] * abs(tN)  # only sizes the path
+        down = [(x, 0.0, 0.0) for x in np.linspace(0.0, eN, 200)]
+        side = [(eN, x, 0.0) for x in np.linspace(0.0, 3.0 * cap / (a * E0), 6001)[1:]]
+        ts, _ = march(mat, down + side)
+        np.testing.assert_allclose(ts[-1, 0], tN, rtol=1e-12)
+        assert ts[-1, 1] == ts[-2, 1]  # sliding at the cap
+        return ts[-1, 1]
+
+    d = 1e-3
+    assert abs((plateau(-d) - plateau(0.0)) / d - mat["mu0"]) < 1e-5
+    assert abs((plateau(-12 * sN0) - plateau(-10 * sN0)) / (2 * sN0) - mat["mu_inf"]) < 1e-4
+
+
 @pytest.mark.parametrize("eN", [1e-160, 1e-200, 5e-324])
 def test_vanishing_tensile_strain_is_elastic_not_nan(eN):
     """At e_N > 0 so small that its square underflows, t / e is 0/0; the law's elastic limit t = E e
