@@ -240,3 +240,48 @@ def test_prescribed_ramp_reaction_is_newton_on_a_rigid_body():
     Ek = 0.5 * M * float(v @ v)
     np.testing.assert_allclose(Wkin, Ek, rtol=1e-9)
     assert abs(Wext - Ek) <= Ek / n_ramp
+
+
+def test_strain_perturbation_is_a_new_reference_not_an_increment():
+    """Sec. 5 perturbations (reading: the perturbed state is the reference of the next strain
+    increment; tractions and velocities are kept).  Two particles at rest, the facet stretched
+    elastically to half its peak with the matching traction; J is then displaced along the axis by
+    0.3 of the peak strain.  The next step's traction moves only by the step's own strain increment
+    (dt^2 F / m, four orders below the jump), not by E0 times the perturbation.  e_max, the largest
+    effective strain reached, follows the total strain to 0.8 of the peak."""
+    l, m = 3.0, 1e-6
+    spec = two_particle(l)
+    o = oracle.Oracle(spec, MAT, 1e-7, mass=np.full(2, m), inertia=np.full((2, 3), 1e-7))
+    e0 = MAT["sigma_t"] / MAT["E0"]
+    q = np.zeros((2, 6))
+    q[1, 0] = 0.5 * e0 * l
+    t0 = MAT["E0"] * 0.5 * e0
+    o.set_state(q, np.zeros((2, 6)), np.array([[t0, 0.0, 0.0, 0.0, 0.5 * e0]]))
+    dq = np.zeros((2, 6))
+    dq[1, 0] = 0.3 * e0 * l
+    o.perturb(dq)
+    o.step(1)
+    _, _, h, _ = o.get_state()
+    jump = MAT["E0"] * 0.3 * e0
+    assert abs(h[0, 0] - t0) < 1e-2 * jump, (h[0, 0], t0, jump)
+    assert abs(h[0, 4] - 0.8 * e0) < 1e-3 * e0
+
+
+def test_set_bc_takes_the_constrained_velocities_at_once():
+    """Switching boundary conditions mid-run: a newly prescribed DOF moves at bc_vel ramp(t) from the
+    switch on (reported velocity and kinetic energy), a newly fixed one stops."""
+    spec = two_particle(3.0)
+    bc = workloads.free_bc(2)
+    bc.v0[:, 0] = [2.0, -1.0]
+    o = oracle.Oracle(spec, EL, 1e-7, bc, mass=np.full(2, 1e-6), inertia=np.full((2, 3), 1e-7))
+    o.step(10)
+    nb = workloads.free_bc(2)
+    nb.mask[0, :] = workloads.FIXED
+    nb.mask[1, 0] = workloads.PRESCRIBED
+    nb.vel[1, 0] = 7.0
+    nb.ramp_time = 0.0
+    o.set_bc(nb)
+    _, v, _, _ = o.get_state()
+    assert np.all(v[0] == 0.0) and v[1, 0] == 7.0
+    (_, _, Wk, _), _ = o.energy()
+    np.testing.assert_allclose(Wk, 0.5 * 1e-6 * 49.0 + 0.5 * 1e-7 * float(v[1, 3:] @ v[1, 3:]) + 0.5 * 1e-6 * float(v[1, 1:3] @ v[1, 1:3]), rtol=1e-12)

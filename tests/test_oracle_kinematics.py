@@ -172,6 +172,12 @@ def test_crack_opening_zero_while_elastic_and_equal_to_jump_when_separated():
     o.set_state(q, np.zeros((2, 6)), np.array([[0.0, 0, 0, 0, 1.0]]))
     w, _ = o.metrics()
     assert abs(w[0] - math.hypot(0.02, 0.01)) < 1e-14
+    # compacted past sigma_c0: inelastic normal strain e_N - t_N / E0 = -e_c0 < 0 opens no crack
+    ec0 = MAT["sigma_c0"] / MAT["E0"]
+    q[1, :3] = [-2.0 * ec0 * l, 0.0, 0.0]
+    o.set_state(q, np.zeros((2, 6)), np.array([[-MAT["sigma_c0"], 0, 0, 0, 0.0]]))
+    w, _ = o.metrics()
+    assert w[0] == 0.0
 
 
 def test_volumetric_strain_metric_is_trace_over_three(cube):

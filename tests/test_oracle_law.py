@@ -170,11 +170,43 @@ def test_deviatoric_softens_hardening_modulus():
 
     h_hyd, _ = hardening_slope(1.0)
     assert abs(h_hyd - Hc0) < 1e-6 * Hc0
+    # r_DV = 0.5 s / (e_V0 + s) stays below k_c1 = 1 on the whole path: no softening of H_c yet
+    assert MAT["kc1"] == 1.0
+    h_mild, _ = hardening_slope(1.5)
+    assert abs(h_mild - Hc0) < 1e-6 * Hc0
     h_dev, tN = hardening_slope(200.0)
     assert Hc1 <= h_dev < 1.01 * Hc1
     # plateau sigma_c0 while -e_DV < e_c0 even though the facet strain is far beyond e_c0
     _, tN_short = hardening_slope(200.0)
     assert abs(tN_short[int(0.5 * len(tN_short))] - sc0) < 1e-9 * sc0
+
+
+def test_boundary_without_compaction_stays_at_sigma_c0():
+    """App. A.2: while the tetrahedron does not compact (-e_DV <= 0), sigma_bc = sigma_c0 however far
+    the facet itself is compressed (no hardening branch is reached)."""
+    ec0 = MAT["sigma_c0"] / MAT["E0"]
+    s = np.linspace(0.0, 4.0 * ec0, 4001)
+    for eV in (0.0, 2e-4):
+        ts, _ = march(MAT, [(-x, 0.0, 0.0) for x in s], eV_of=lambda e: np.full_like(e[0], eV))
+        tN = -ts[:, 0]
+        np.testing.assert_allclose(tN, np.minimum(MAT["E0"] * s, MAT["sigma_c0"]), rtol=1e-12)
+
+
+def test_beta_one_makes_the_boundary_a_function_of_e_N_alone():
+    """App. A.2 with beta = 1: e_DV = e_V + (e_N - e_V) = e_N, so with the deviatoric softening of
+    H_c switched off (k_c1 above any r_DV) the compressive response along e_N does not depend on the
+    tetrahedron's volumetric strain: a facet compressed three times faster than its tetrahedron follows
+    the hydrostatic curve point by point."""
+    mat = dict(MAT, beta=1.0, kc1=1e9)
+    ec1 = mat["kc0"] * mat["sigma_c0"] / mat["E0"]
+    s = np.linspace(0.0, 1.5 * ec1, 15001)
+    hyd, _ = march(mat, [(-x, 0.0, 0.0) for x in s], eV_of=lambda e: e[0])
+    dev, _ = march(mat, [(-x, 0.0, 0.0) for x in s], eV_of=lambda e: e[0] / 3.0)
+    assert -hyd[-1, 0] > mat["sigma_c0"] * 1.5  # the path went well into hardening
+    np.testing.assert_allclose(dev[:, 0], hyd[:, 0], rtol=1e-12)
+    # with beta = 0 the same two paths differ (e_DV = e_V), which is what makes the check bite
+    h0, _ = march(dict(mat, beta=0.0), [(-x, 0.0, 0.0) for x in s], eV_of=lambda e: e[0] / 3.0)
+    assert abs(h0[-1, 0] - hyd[-1, 0]) > 0.05 * abs(hyd[-1, 0])
 
 
 def test_friction_cap_and_initial_slope_mu0():
@@ -226,4 +258,5 @@ def test_vanishing_tensile_strain_is_elastic_not_nan(eN):
     must come out (a loading wave leaves such strains ahead of its front)."""
     e = np.array([eN, 0.0, 0.0])
     t, em = oracle.facet_law(MAT, L_EDGE, e, e, 0.0, np.zeros(3), 0.0)
-    assert np.all(np.isfinite(t)) and t[0] == MAT["E0"] * eN and em >= 0.0
+    assert np.all(np.isfinite(t)) and t[0] == MAT["E0"] * eN
+    assert em == math.sqrt(eN * eN)  # e_max takes the (vanishing) effective strain, |e_N| here
