@@ -143,3 +143,57 @@ def test_full_size_uniaxial_tension_one_step():
 def test_max_size_confined_compression_one_step():
     """The largest workload (12.5M facets), one step from an oracle state, both precisions."""
     _full_size_one_step("confined_compression", 4, 2000.0, [("fp64", 1e-10), ("mixed", 2e-5)])
+
+
+@pytest.fixture(scope="module")
+def hanging():
+    """12 mm cube, bottom face fixed, under constant external nodal forces: a body force m g along +z
+    (g = 1e8 mm/s^2, enough to crack the facets near the support) and 0.5 N along x on every top-face
+    particle.  The oracle runs 300 steps."""
+    spec = specimen.shuffled(specimen.make_cube_specimen(12.0, 2.0, 4.0, 300, seed=24), seed=6)
+    bc = workloads.free_bc(spec.n_particles)
+    bc.mask[spec.face_nodes(2, 0), :] = workloads.FIXED
+    o = oracle.Oracle(spec, MAT, 1e-7, bc)
+    f = np.zeros((spec.n_particles, 6))
+    f[:, 2] = o.geometry()["mass"][:, 0] * 1e8
+    f[spec.face_nodes(2, 1), 0] = 0.5
+    dt = 0.9 * o.critical_dt()
+    o = oracle.Oracle(spec, MAT, dt, bc, f_ext=f)
+    o.step(300)
+    return spec, bc, f, dt, o
+
+
+def test_external_force_trajectory_fp64(hanging):
+    spec, bc, f, dt, o = hanging
+    h = o.get_state()[2]
+    assert np.sum(h[:, 4] > 1.5 * MAT["sigma_t"] / MAT["E0"]) > 300, "facets must have cracked"
+    m = ldpm.Model(spec, MAT, precision="fp64", dt=dt, bc=bc, f_ext=f)
+    m.step(300)
+    qg, vg, hg, _ = m.get_state()
+    qo, vo, ho, _ = o.get_state()
+    assert nrel(qg, qo) <= 1e-8 and nrel(vg, vo) <= 1e-8 and nrel(hg, ho) <= 1e-7, (nrel(qg, qo), nrel(hg, ho))
+    eg, rg = m.energy()
+    eo, ro = o.energy()
+    assert eo[0] > 0 and nrel(eg[:3], eo[:3]) <= 1e-8 and nrel(rg, ro) <= 1e-7, (eg, eo, rg, ro)
+    m.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("mixed", 2e-5)])
+def test_external_force_one_step(hanging, prec, tol):
+    spec, bc, f, dt, o = hanging
+    q, v, h5, st = o.get_state()
+    o2 = oracle.Oracle(spec, MAT, dt, bc, f_ext=f)
+    o2.set_state(q, v, h5, st)
+    o2.step(1)
+    qo, vo, _, _ = o2.get_state()
+    _, fo = o2.facet_forces()
+    m = ldpm.Model(spec, MAT, precision=prec, dt=dt, bc=bc, f_ext=f)
+    m.set_state(q, v, h5, st)
+    m.step(1)
+    qg, vg, _, _ = m.get_state()
+    _, fg = m.facet_forces()
+    assert nrel(fg, fo) <= tol and nrel(vg, vo) <= tol and nrel(qg, qo) <= tol, (nrel(fg, fo), nrel(vg, vo))
+    eg, _ = m.energy()
+    eo, _ = o2.energy()
+    assert nrel(eg[:1], eo[:1]) <= tol  # the external work of the step
+    m.close()

@@ -202,6 +202,26 @@ def test_objective_is_time_mean_of_reported_reactions_and_state_is_kept(cube):
     np.testing.assert_allclose(J, np.mean(Rz), rtol=1e-12)
 
 
+def test_objective_counts_fixed_and_prescribed_seeds(cube):
+    """The objective sums seeded reactions over every constrained DOF, fixed ones included: seeds on
+    the bottom face's fixed u_x, u_z and the top face's prescribed u_x, u_z give the time mean of the
+    matching combination of the reported reaction sums (fixed u_x, u_z: bottom face only here)."""
+    spec, bc, dt, _, K = cube
+    top, bot = spec.face_nodes(2, 1), spec.face_nodes(2, 0)
+    seed = np.zeros((spec.n_particles, 6))
+    seed[top, 2], seed[top, 0], seed[bot, 2], seed[bot, 0] = 1.0, 0.3, -0.5, 0.25
+    o = oracle.Oracle(spec, MAT, dt, bc)
+    J, _ = o.tangent(K // 3, seed)
+    comb = []
+    for _ in range(K // 3):
+        o.step(1)
+        R = o.energy()[1]
+        comb.append(R[8] + 0.3 * R[6] - 0.5 * R[2] + 0.25 * R[0])
+    np.testing.assert_allclose(J, np.mean(comb), rtol=1e-12)
+    R = o.energy()[1]
+    assert abs(R[2]) > 0.1 * abs(R[8]) and abs(R[0]) > 0.0  # the fixed faces do carry load
+
+
 def test_cube_tangent_matches_central_differences(cube):
     spec, bc, dt, seed, K = cube
     o = oracle.Oracle(spec, MAT, dt, bc)

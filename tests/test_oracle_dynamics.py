@@ -285,3 +285,61 @@ def test_set_bc_takes_the_constrained_velocities_at_once():
     assert np.all(v[0] == 0.0) and v[1, 0] == 7.0
     (_, _, Wk, _), _ = o.energy()
     np.testing.assert_allclose(Wk, 0.5 * 1e-6 * 49.0 + 0.5 * 1e-7 * float(v[1, 3:] @ v[1, 3:]) + 0.5 * 1e-6 * float(v[1, 1:3] @ v[1, 1:3]), rtol=1e-12)
+
+
+def test_constant_external_force_free_flight():
+    """Constant external forces f_ext, the same on both particles: the pair accelerates rigidly at
+    a = f / m, which central difference integrates exactly (q_n = a (n dt)^2 / 2, v_n = a n dt), the
+    facet stays unstrained, and the external work f . q equals the kinetic energy."""
+    m, dt, n = 1e-6, 1e-7, 50
+    spec = two_particle(3.0)
+    f = np.zeros((2, 6))
+    f[:, :3] = [2.0, -1.0, 0.5]
+    o = oracle.Oracle(spec, MAT, dt, mass=np.full(2, m), inertia=np.full((2, 3), 1e-7), f_ext=f)
+    o.step(n)
+    q, v, h, _ = o.get_state()
+    a = f[0, :3] / m
+    np.testing.assert_allclose(q[:, :3], np.tile(0.5 * a * (n * dt) ** 2, (2, 1)), rtol=1e-12)
+    np.testing.assert_allclose(v[:, :3], np.tile(a * n * dt, (2, 1)), rtol=1e-12)
+    assert np.all(q[:, 3:] == 0.0) and np.all(h == 0.0)
+    (Wext, Wint, Wkin, err), R = o.energy()
+    np.testing.assert_allclose(Wext, float((f * q).sum()), rtol=1e-12)
+    np.testing.assert_allclose(Wkin, Wext, rtol=1e-12)
+    assert Wint == 0.0 and err < 1e-9 and np.all(R == 0.0)
+
+
+def test_energy_balance_restarts_at_set_state():
+    """set_state starts a new energy balance: W_ext = W_int = 0 and the supplied kinetic energy is
+    that of the velocities just set.  A free elastic cube created with velocities v0 and then set to
+    2 v0 keeps its balance (W_kin + W_int = W_kin at the set) over the following steps."""
+    spec = specimen.make_cube_specimen(8.0, 2.0, 4.0, 60, seed=1)
+    bc = workloads.free_bc(spec.n_particles)
+    # a smooth field (low modes, where the trapezoid energy sums are accurate)
+    z, x = spec.x[:, 2] / spec.edge, spec.x[:, 0] / spec.edge
+    bc.v0[:, 0] = np.sin(np.pi * z)
+    bc.v0[:, 1] = 0.5 * np.cos(np.pi * x)
+    o = oracle.Oracle(spec, EL, 1e-7, bc)
+    dt = 0.5 * o.critical_dt()
+    o = oracle.Oracle(spec, EL, dt, bc)
+    o.step(40)
+    q = np.zeros((spec.n_particles, 6))
+    o.set_state(q, 2.0 * bc.v0, np.zeros((spec.n_facets, 5)), 0)
+    (_, _, Wk0, err0), _ = o.energy()
+    assert err0 == 0.0
+    o.step(300)
+    (Wext, Wint, Wkin, err), _ = o.energy()
+    assert Wext == 0.0 and Wint > 0.05 * Wkin
+    assert abs(Wkin + Wint - Wk0) < 1e-2 * Wk0 and err < 1.0
+
+
+def test_kinetic_energy_counts_rotations():
+    """W_kin = sum over DOFs of m v^2 / 2 with the rotary inertia on the rotational DOFs."""
+    spec = two_particle(3.0)
+    I = np.array([[1e-7, 2e-7, 3e-7], [4e-7, 5e-7, 6e-7]])
+    o = oracle.Oracle(spec, EL, 1e-7, mass=np.full(2, 1e-6), inertia=I)
+    v = np.zeros((2, 6))
+    v[0, 3:] = [1.0, -2.0, 0.5]
+    v[1, 0] = 3.0
+    o.set_state(np.zeros((2, 6)), v, np.zeros((1, 5)))
+    (_, _, Wkin, _), _ = o.energy()
+    np.testing.assert_allclose(Wkin, 0.5 * (I[0] * v[0, 3:] ** 2).sum() + 0.5 * 1e-6 * 9.0, rtol=1e-14)

@@ -188,3 +188,45 @@ def test_volumetric_strain_metric_is_trace_over_three(cube):
     o.set_state(affine_q(spec, eps), np.zeros((spec.n_particles, 6)), np.zeros((spec.n_facets, 5)))
     _, eV = o.metrics()
     np.testing.assert_allclose(eV, np.trace(eps) / 3.0, rtol=1e-10)
+
+
+def test_state_exchange_tangential_traction_in_world_frame():
+    """History exchange (get_state / set_state) stores the tangential traction as a world vector
+    t_M m + t_L l.  Two particles on the x axis; J is driven sideways along d = (0, 1, 2) / sqrt(5)
+    (a direction with parts along both tangents of any frame) with I fixed and no rotation, an
+    elastic shear of 0.2 of the cracking strain.  The stored vector is alpha E0 (delta / l) d, the
+    normal traction is zero; set_state then get_state returns it unchanged, and the facet force is
+    rebuilt from it as F = A (t_N n + t_T) on I with -F on J (Eq. (2a)), the lumped forces following."""
+    from paper_2603_13190_gb300 import workloads
+    from paper_2603_13190_gb300.specimen import Specimen
+    l, h, dt, n = 3.0, 2.0, 1e-7, 40
+    x = np.array([[0.0, 0.0, 0.0], [l, 0.0, 0.0]])
+    vtx = np.array([[l / 2, -h / 3, -h / 3, l / 2, 2 * h / 3, -h / 3, l / 2, -h / 3, 2 * h / 3]])
+    spec = Specimen(x=x, diameter=np.ones(2), tets=np.zeros((0, 4), np.int32), facet_pi=np.array([0], np.int32),
+                    facet_pj=np.array([1], np.int32), facet_tet=np.array([-1], np.int32), facet_vtx=vtx, edge=l,
+                    d_min=1.0, d_max=1.0)
+    d = np.array([0.0, 1.0, 2.0]) / np.sqrt(5.0)
+    e0 = MAT["sigma_t"] / MAT["E0"]
+    delta = 0.2 * e0 * l
+    bc = workloads.free_bc(2)
+    bc.mask[:, :] = workloads.FIXED
+    bc.mask[1, :3] = workloads.PRESCRIBED
+    bc.vel[1, :3] = d * delta / (n * dt)
+    kw = dict(mass=np.full(2, 1e-6), inertia=np.full((2, 3), 1e-7))
+    o = oracle.Oracle(spec, MAT, dt, bc, **kw)
+    o.step(n)
+    q, v, h5, st = o.get_state()
+    np.testing.assert_allclose(q[1, :3], delta * d, rtol=1e-12)
+    tT = MAT["alpha"] * MAT["E0"] * delta / l * d
+    assert abs(h5[0, 0]) < 1e-12 * np.abs(tT).max()
+    np.testing.assert_allclose(h5[0, 1:4], tT, rtol=1e-10, atol=1e-14 * np.abs(tT).max())
+    # round trip through a fresh model, and forces rebuilt from the history
+    o2 = oracle.Oracle(spec, MAT, dt, bc, **kw)
+    o2.set_state(q, v, h5, st)
+    np.testing.assert_allclose(o2.get_state()[2], h5, rtol=1e-13, atol=1e-15 * np.abs(tT).max())
+    A = o2.geometry()["area"][0]
+    F3, f6 = o2.facet_forces()
+    F = A * (h5[0, 0] * np.array([1.0, 0.0, 0.0]) + h5[0, 1:4])
+    np.testing.assert_allclose(F3[0], F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
+    np.testing.assert_allclose(f6[0, :3], F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
+    np.testing.assert_allclose(f6[1, :3], -F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
