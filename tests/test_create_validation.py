@@ -112,3 +112,17 @@ def test_tetrahedron_checks(big):
     tets = big.tets.copy()
     tets[6000, 3] = tets[6000, 1]
     assert "tet 6000: repeated particle" in _msg(dataclasses.replace(big, tets=tets))
+
+
+def test_empty_specimen_and_empty_batch_are_rejected():
+    """The smallest specimen the step accepts is one tetrahedron with its 12 facets; an empty one is
+    rejected with LDPM_E_BAD_GEOMETRY before any CUDA call, and a batch of no specimens with
+    LDPM_E_INVALID_ARG."""
+    one = specimen.single_tet_specimen()
+    empty = dataclasses.replace(one, tets=np.zeros((0, 4), np.int32), facet_pi=np.zeros(0, np.int32),
+                                facet_pj=np.zeros(0, np.int32), facet_tet=np.zeros(0, np.int32),
+                                facet_vtx=np.zeros((0, 9)))
+    assert "need N >= 4, T >= 1 and F == 12 T" in _msg(empty)
+    with pytest.raises(ldpm.LdpmError) as ei:
+        ldpm.ldpm_batch_create([], [])
+    assert ei.value.code == -1, str(ei.value)
