@@ -583,6 +583,13 @@ int update_law(ldpm_ctx *h)
         std::vector<LawConst<float>> law(h->sp.size());
         for (size_t s = 0; s < h->sp.size(); ++s) law_const<float>(h->sp[s].mat, h->sp[s].dt, law[s]);
         CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(law[0]), cudaMemcpyHostToDevice));
+        if (std::memcmp(&h->dm.law1, &law[0], sizeof(law[0])) != 0) {
+            // the copy travels in the kernel parameters: captured launches hold the old one
+            CU(cudaStreamSynchronize(h->stream));
+            for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+            h->graphs.clear();
+            h->dm.law1 = law[0];
+        }
     } else {
         std::vector<LawConst<double>> law(h->sp.size());
         for (size_t s = 0; s < h->sp.size(); ++s) law_const<double>(h->sp[s].mat, h->sp[s].dt, law[s]);

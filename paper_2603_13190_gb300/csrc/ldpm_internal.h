@@ -92,6 +92,7 @@ struct DeviceModel {
     int32_t *row = nullptr;
     int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)
     void *law = nullptr;            // LawConst<R>[n_spec]
+    LawConst<float> law1{};         // mixed mode, one specimen: lawc[0] again, read from the kernel parameters
     SpecDyn *spec = nullptr;        // [n_spec]
     int64_t *step = nullptr;        // step counter (one for all specimens)
     int32_t *flag = nullptr;        // non-finite state seen

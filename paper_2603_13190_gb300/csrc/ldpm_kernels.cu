@@ -166,7 +166,9 @@ __device__ __forceinline__ void stage_vertex(const DeviceModel &m, const void *_
 
 // One facet (tetrahedron j of the tile, slot 0..11, global facet f): kinematics, law, history, force,
 // and its contributions to its two vertices in cs[12] (zeros when the facet is not live).
-template <class R, int MODE, bool PF>
+// S1: one specimen in mixed mode, law constants taken from m.law1 (the kernel parameters) instead of
+// the global array; see facet_warp_kernel.
+template <class R, int MODE, bool PF, bool S1 = false>
 __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, int j, int slot, int64_t f, bool live,
                                           const R4<R> &g, const R4<R> &h, const R4<R> &pp,
                                           const R (*sv)[Stride<R>::row], const R *seV, R cs[12])
@@ -199,10 +201,16 @@ __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, in
     const V3<R> ca = {g.x, g.y, g.z};
     const V3<R> cb = ca - d;
     R tN, tM, tL, emax;
-    const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;  // specimens are padded to 32 tetrahedra
+    const LawConst<R> *lsrc;
+    if constexpr (S1 && sizeof(R) == 4) {
+        lsrc = reinterpret_cast<const LawConst<R> *>(&m.law1);
+    } else {
+        const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;  // specimens are padded to 32 tetrahedra
+        lsrc = lawc + sp;
+    }
     LawConst<R> cpf;
-    if constexpr (PF) cpf = facet_params(lawc[sp], pp.x, pp.y, pp.z);
-    const LawConst<R> &c = PF ? cpf : lawc[sp];
+    if constexpr (PF) cpf = facet_params(*lsrc, pp.x, pp.y, pp.z);
+    const LawConst<R> &c = PF ? cpf : *lsrc;
     if (MODE == FACET_FROM_HIST) {
         tN = h.x;
         tM = h.y;
@@ -360,10 +368,15 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 // components 2q, 2q+1 of vertex v of tetrahedron j (task t = 12 j + 3 v + q) then reads word 2t of
 // each plane: contiguous for the lanes, free of bank conflicts.  Planes are kPlane words apart (192
 // plus 2, so that the facets' stores into different planes fall on different banks).
+// With one specimen (S1) the law constants are read from the kernel's own parameters (m is a
+// __grid_constant__, so taking its address makes no copy): there they are operands of the
+// instructions that use them, where the global array costs a load per use and facet (measured on
+// GB300 in the loaded state of 1.82M facets: 43.1 us against 45.2 us).
 constexpr int kTileTets = 8;
 constexpr int kPlane = 6 * 4 * kTileTets + 2;
-template <class R, int MODE, int WPB, bool PF>
-__global__ void __launch_bounds__(32 * WPB) facet_warp_kernel(DeviceModel m, const void *__restrict__ vsrc)
+template <class R, int MODE, int WPB, bool PF, bool S1>
+__global__ void __launch_bounds__(32 * WPB)
+    facet_warp_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc)
 {
     using T4 = R4<R>;
     using V2 = typename VecT<R>::v2;
@@ -406,7 +419,7 @@ __global__ void __launch_bounds__(32 * WPB) facet_warp_kernel(DeviceModel m, con
         const bool live = tet0 + j < m.T && sok[j];
         const int slot = fi - 12 * j;
         R cs[12];
-        facet_one<R, MODE, PF>(m, tet0, j, slot, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs);
+        facet_one<R, MODE, PF, S1>(m, tet0, j, slot, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs);
         if (MODE != FACET_METRIC) {
             // edge e = slot / 2 joins local vertices va < vb; it is the ka-th edge of va and the kb-th
             // of vb (ascending), so this facet is entry 2 ka + slot % 2 of va's order, 2 kb + slot % 2 of vb's
@@ -884,7 +897,11 @@ cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t 
     if (sizeof(R) == 4 && tpb == kTileTets) {
         constexpr int WPB = 2;
         const int64_t tiles = (m.T + kTileTets - 1) / kTileTets;
-        facet_warp_kernel<R, MODE, WPB, PF><<<(unsigned)((tiles + WPB - 1) / WPB), 32 * WPB, 0, s>>>(m, pst);
+        const unsigned nb = (unsigned)((tiles + WPB - 1) / WPB);
+        if (m.n_spec == 1)
+            facet_warp_kernel<R, MODE, WPB, PF, true><<<nb, 32 * WPB, 0, s>>>(m, pst);
+        else
+            facet_warp_kernel<R, MODE, WPB, PF, false><<<nb, 32 * WPB, 0, s>>>(m, pst);
         return cudaGetLastError();
     }
     switch (tpb) {
