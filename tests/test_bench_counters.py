@@ -23,3 +23,28 @@ def test_counters_follow_the_per_unit_formulas():
         assert d["step_bytes"] == d["facet_pass_bytes"] + d["particle_pass_bytes"]
         assert d["adjoint_step_bytes"] == 2 * d["step_bytes"] + d["reverse_facet_pass_bytes"] + \
             d["reverse_particle_pass_bytes"]
+
+
+def test_recorded_traffic_is_tied_to_the_kernel_source(monkeypatch):
+    """`traffic` in the bench line comes from profiles/traffic.json only while the kernel sources hash
+    to the value the capture was taken with; any other source reads as null."""
+    import json
+
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    key = "facet_warp_kernel/uniaxial_tension/mixed"
+    assert key in d and d[key]["bytes_per_launch"] > 0
+    monkeypatch.setattr(bench, "kernel_src_hash", lambda: d[key]["kernel_src_hash"])
+    assert bench.recorded_traffic("facet_warp_kernel", "uniaxial_tension", "mixed") == d[key]["bytes_per_launch"]
+    assert bench.recorded_traffic("no_such_kernel", "uniaxial_tension", "mixed") is None
+    monkeypatch.setattr(bench, "kernel_src_hash", lambda: "0" * 16)
+    assert bench.recorded_traffic("facet_warp_kernel", "uniaxial_tension", "mixed") is None
+    assert bench.fp64_alu_roofline("uniaxial_tension", 1.5) is None
+
+
+def test_fp64_alu_roofline_arithmetic(monkeypatch):
+    """achieved = FP64 flops per launch / launch time, against 152 SMs x 2 DFMA x 2 flop x 2.07 GHz."""
+    monkeypatch.setattr(bench, "recorded_traffic", lambda *a, **k: 9.0e8)
+    r = bench.fp64_alu_roofline("uniaxial_tension", 1.5)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 9.0e8 / 1.5e-3 / 1e12) < 1e-12
+    assert abs(r["peak"] - 1.25856) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
