@@ -595,6 +595,82 @@ def cpu_baseline(spec, wl, bc, dt, budget_s: float = 20.0):
             "sample": "%d explicit steps of the full %d-facet specimen (%.1f s, single thread)" % (n, spec.n_facets, el)}
 
 
+# One oracle process of the all-cores baseline: rebuilds the problem from a saved file, steps once,
+# reports ready, waits for the start line on stdin, then steps until its time budget is spent.
+_ORACLE_WORKER = r"""
+import json, sys, time
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_2603_13190_gb300.specimen import Specimen
+from paper_2603_13190_gb300.workloads import BoundaryConditions
+z = np.load(sys.argv[2])
+a = json.loads(sys.argv[3])
+spec = Specimen(x=z['x'], diameter=z['diameter'], tets=z['tets'], facet_pi=z['facet_pi'], facet_pj=z['facet_pj'],
+                facet_tet=z['facet_tet'], facet_vtx=z['facet_vtx'], edge=a['edge'], d_min=a['d_min'], d_max=a['d_max'])
+bc = BoundaryConditions(mask=z['mask'], vel=z['vel'], ramp_time=a['ramp_time'], v0=z['v0'])
+o = oracle.Oracle(spec, a['material'], a['dt'], bc)
+o.step(1)
+print('ready', flush=True)
+sys.stdin.readline()
+n, t0 = 0, time.perf_counter()
+while time.perf_counter() - t0 < a['budget_s']:
+    o.step(1)
+    n += 1
+print(json.dumps({'steps': n, 'seconds': time.perf_counter() - t0}), flush=True)
+"""
+
+
+def cpu_all_cores(spec, wl, bc, dt, budget_s: float = 10.0, max_procs: int = 16):
+    """The oracle on all host cores: one single-thread oracle process per core, each stepping its own
+    copy of the full specimen over the same time window; the value is the sum of their rates (the
+    host's aggregate throughput on independent copies of the workload; the oracle itself is not
+    parallelised).  Processes are started with subprocess, so none is forked from this one.  Returns
+    None with the reason on any failure."""
+    import tempfile
+
+    cores = os.cpu_count() or 1
+    try:
+        avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+    except (ValueError, OSError):
+        avail_gb = 8.0
+    per_gb = 1.0 + spec.n_facets * 400 / 2 ** 30  # interpreter and libraries, plus the oracle's arrays
+    C = int(max(1, min(cores, max_procs, avail_gb // (2 * per_gb))))
+    procs = []
+    with tempfile.TemporaryDirectory(prefix="oracle_cores_") as d:
+        f = os.path.join(d, "problem.npz")
+        np.savez(f, x=spec.x, diameter=spec.diameter, tets=spec.tets, facet_pi=spec.facet_pi, facet_pj=spec.facet_pj,
+                 facet_tet=spec.facet_tet, facet_vtx=spec.facet_vtx, mask=bc.mask, vel=bc.vel, v0=bc.v0)
+        a = json.dumps({"edge": spec.edge, "d_min": spec.d_min, "d_max": spec.d_max, "ramp_time": bc.ramp_time,
+                        "material": dict(wl.material), "dt": dt, "budget_s": budget_s})
+        try:
+            for _ in range(C):
+                procs.append(subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, ROOT, f, a], cwd=ROOT,
+                                              stdin=subprocess.PIPE, stdout=subprocess.PIPE,
+                                              stderr=subprocess.DEVNULL, text=True))
+            for pr in procs:
+                if pr.stdout.readline().strip() != "ready":
+                    raise RuntimeError("an oracle process did not start")
+            for pr in procs:
+                pr.stdin.write("go\n")
+                pr.stdin.flush()
+            res = []
+            for pr in procs:
+                out, _ = pr.communicate(timeout=budget_s + 120)
+                res.append(json.loads(out.strip().splitlines()[-1]))
+        except Exception as e:  # the GPU figures stand on their own: report why this one is missing
+            for pr in procs:
+                if pr.poll() is None:
+                    pr.kill()
+            return {"value": None, "reason": "%s: %s" % (type(e).__name__, e)}
+    rate = sum(spec.n_facets * r["steps"] / r["seconds"] for r in res)
+    steps = [r["steps"] for r in res]
+    return {"value": rate, "unit": UNIT, "cores": C, "kind": "oracle",
+            "sample": "%d concurrent single-thread oracle processes (%d host cores), each stepping its own copy of "
+                      "the full %d-facet specimen for %.0f s (%d-%d steps each); sum of their rates"
+                      % (C, cores, spec.n_facets, budget_s, min(steps), max(steps))}
+
+
 def run_reference(args, rank, world):
     """The oracle as the reference arm: same workload, metric and unit, timed on the host cores."""
     if rank != 0:
@@ -779,6 +855,7 @@ def main():
     if rank == 0:
         if world == 1 and not args.no_cpu_baseline:
             res["cpu_baseline"] = cpu_baseline(spec, wl, bc, dt)
+            res["cpu_all_cores"] = cpu_all_cores(spec, wl, bc, dt)
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -48,3 +48,14 @@ def test_fp64_alu_roofline_arithmetic(monkeypatch):
     assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - 9.0e8 / 1.5e-3 / 1e12) < 1e-12
     assert abs(r["peak"] - 1.25856) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
+
+
+def test_cpu_all_cores_sums_concurrent_oracle_processes():
+    """The all-cores oracle figure: independent oracle processes over one time window, rates summed."""
+    from paper_2603_13190_gb300 import workloads
+
+    wl = workloads.WORKLOADS["elastic_vibration"]
+    spec = wl.specimen()
+    r = bench.cpu_all_cores(spec, wl, workloads.workload_bc(wl.name, spec), 1e-7, budget_s=0.5, max_procs=2)
+    assert r["value"] > 0 and r["kind"] == "oracle" and 1 <= r["cores"] <= 2, r
+    assert "concurrent single-thread oracle processes" in r["sample"]
