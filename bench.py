@@ -648,9 +648,14 @@ def cpu_all_cores(spec, wl, bc, dt, budget_s: float = 10.0, max_procs: int = 16)
                 procs.append(subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, ROOT, f, a], cwd=ROOT,
                                               stdin=subprocess.PIPE, stdout=subprocess.PIPE,
                                               stderr=subprocess.DEVNULL, text=True))
+            import select
+
+            deadline = time.monotonic() + 300.0
             for pr in procs:
-                if pr.stdout.readline().strip() != "ready":
-                    raise RuntimeError("an oracle process did not start")
+                left = deadline - time.monotonic()
+                if left <= 0 or not select.select([pr.stdout], [], [], left)[0] or \
+                        pr.stdout.readline().strip() != "ready":
+                    raise RuntimeError("an oracle process did not get ready")
             for pr in procs:
                 pr.stdin.write("go\n")
                 pr.stdin.flush()
