@@ -630,10 +630,15 @@ def cpu_all_cores(spec, wl, bc, dt, budget_s: float = 10.0, max_procs: int = 16)
     import tempfile
 
     cores = os.cpu_count() or 1
-    try:
-        avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
-    except (ValueError, OSError):
-        avail_gb = 8.0
+    avail_gb = 8.0
+    try:  # memory the kernel can hand out without swapping (free pages plus reclaimable cache)
+        with open("/proc/meminfo") as mi:
+            avail_gb = next(int(l.split()[1]) for l in mi if l.startswith("MemAvailable:")) / 2 ** 20
+    except (OSError, StopIteration, ValueError):
+        try:
+            avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
+        except (ValueError, OSError):
+            pass
     per_gb = 1.0 + spec.n_facets * 400 / 2 ** 30  # interpreter and libraries, plus the oracle's arrays
     C = int(max(1, min(cores, max_procs, avail_gb // (2 * per_gb))))
     procs = []
