@@ -267,6 +267,55 @@ MUTANTS = [
     ('dir_block_offset',
      'const size_t row = (size_t)(d0 + w) * F + k;',
      'const size_t row = (size_t)w * F + k;'),
+    # the derivative rules, the ramp's start, the elastic responses, create and error reporting
+    ('dual_exp_rule',
+     'for (int i = 0; i < D; ++i) r.d[i] = r.v * a.d[i];',
+     'for (int i = 0; i < D; ++i) r.d[i] = a.d[i];'),
+    ('dual_sin_rule',
+     'for (int i = 0; i < D; ++i) r.d[i] = c * a.d[i];',
+     'for (int i = 0; i < D; ++i) r.d[i] = -c * a.d[i];'),
+    ('dual_product_rule',
+     'r.d[i] = a.d[i] * b.v + a.v * b.d[i];',
+     'r.d[i] = a.d[i] * b.v;'),
+    ('dual_fabs_no_flip',
+     'template <int D> Dual<D> fabs(const Dual<D> &a) { return a.v < 0.0 ? -a : a; }',
+     'template <int D> Dual<D> fabs(const Dual<D> &a) { return a; }'),
+    ('ramp_no_lower_clamp',
+     '    if (r < 0.0) r = 0.0;',
+     ';'),
+    ('ramp_zero_time_is_zero',
+     'if (M->ramp_time <= 0.0) return 1.0;',
+     'if (M->ramp_time <= 0.0) return 0.0;'),
+    ('elastic_flag_shear_no_alpha',
+     '        /* Sec. 2: t = E e with E = E0 diag(1, alpha, alpha). */\n        t_new[0] = E0 * e[0];\n        t_new[1] = alpha * E0 * e[1];',
+     '        /* Sec. 2: t = E e with E = E0 diag(1, alpha, alpha). */\n        t_new[0] = E0 * e[0];\n        t_new[1] = E0 * e[1];'),
+    ('tiny_strain_shear_no_alpha',
+     '             * path is E0, so a vanishing effective strain responds elastically, t = E e. */\n            t_new[0] = E0 * e[0];\n            t_new[1] = alpha * E0 * e[1];',
+     '             * path is E0, so a vanishing effective strain responds elastically, t = E e. */\n            t_new[0] = E0 * e[0];\n            t_new[1] = E0 * e[1];'),
+    ('tet_volume_signed',
+     'double vol = fabs(det) / 6.0;',
+     'double vol = det / 6.0;'),
+    ('create_Wkin0_dropped',
+     '    M->W_kin0 = 0.0;\n    for (size_t i = 0; i < n6; ++i) M->W_kin0 += 0.5 * M->mass[i] * M->v[i] * M->v[i];\n    return M;',
+     '    M->W_kin0 = 0.0;\n    return M;'),
+    ('facet_pass_no_e_prev_update',
+     '            T.e_prev[3 * k + a] = e[a];',
+     '            ;'),
+    ('march_total_not_increment',
+     'double de[3] = {e[0] - e_prev[0], e[1] - e_prev[1], e[2] - e_prev[2]};',
+     'double de[3] = {e[0], e[1], e[2]};'),
+    ('step_nonfinite_not_reported',
+     '        if (!isfinite(M->q[i]) || !isfinite(M->v[i])) return -5;',
+     '        ;'),
+    ('tangent_nonfinite_not_reported',
+     'if (!isfinite(value_of(q[i])) || !isfinite(value_of(v[i]))) rc = -5;',
+     ';'),
+    ('v0_fixed_not_zeroed',
+     '        M->v[i] = v0 ? v0[i] : 0.0;\n        if (M->bc_mask[i] == 1) M->v[i] = 0.0;',
+     '        M->v[i] = v0 ? v0[i] : 0.0;'),
+    ('kick_uses_mass_of_next_dof',
+     'T.v[i] = vh[i] + 0.5 * dt * (M->f_ext[i] + T.f_asm[i]) / M->mass[i];',
+     'T.v[i] = vh[i] + 0.5 * dt * (M->f_ext[i] + T.f_asm[i]) / M->mass[i - i % 6];'),
 ]
 
 

@@ -260,3 +260,32 @@ def test_cube_tangent_matches_central_differences(cube):
     assert np.count_nonzero(dJ[single][2::3]) >= 2, "softening facets must have a sigma_t derivative"
     assert np.all(np.abs(dJ[single] - fd[single]) <= 2e-3 * np.abs(fd[single]) + 1e-5 * big)
     np.testing.assert_allclose(dJ[dense], fd[dense], rtol=1e-3)
+
+
+def test_law_jacobian_where_deviatoric_softening_acts():
+    """App. A.2 with the facet compressed well past its tetrahedron (e_D < 0, r_DV > k_c1): H_c then
+    depends on |e_D|, so the derivative passes through |x|' = sign(x) at a negative argument.  The
+    point lies on the linear hardening boundary; the Jacobian matches central differences."""
+    n = 40
+    path = np.stack([np.linspace(0, -1.4e-2, n), np.linspace(0, 1e-4, n), np.zeros(n)], 1)
+    eV = np.linspace(0, -5e-3, n)
+    x = law_point(path, eV, 35, MAT)
+    e_N, e_V = x[0], x[6]
+    eD = e_N - e_V
+    eV0 = MAT["kc3"] * MAT["sigma_c0"] / MAT["E0"]
+    rDV = -abs(eD) / (e_V - eV0)
+    ec0 = MAT["sigma_c0"] / MAT["E0"]
+    assert eD < 0 and rDV > MAT["kc1"] + 0.3 and ec0 < -e_V < MAT["kc0"] * ec0
+    out, jac = oracle.facet_law_jacobian(MAT, L_FACET, x)
+    assert out[0] < -1.01 * MAT["sigma_c0"]
+    for h in (1e-5, 1e-6):
+        fd = np.zeros((4, 14))
+        for c in range(14):
+            hh = h * max(abs(x[c]), SCALE[c])
+            xp, xm = x.copy(), x.copy()
+            xp[c] += hh
+            xm[c] -= hh
+            fd[:, c] = (oracle.facet_law_jacobian(MAT, L_FACET, xp)[0] - oracle.facet_law_jacobian(MAT, L_FACET, xm)[0]) / (2 * hh)
+        assert np.abs(fd - jac).max() <= 1e-7 * np.abs(jac).max(), (h, np.abs(fd - jac).max())
+    # the response does depend on e_D there (the softened H_c): moving e_N alone moves t_N
+    assert abs(jac[0, 0]) > 0 and abs(jac[0, 6]) > 0

@@ -229,6 +229,8 @@ def test_prescribed_ramp_reaction_is_newton_on_a_rigid_body():
     bc.ramp_time = n_ramp * dt
     o = oracle.Oracle(spec, MAT, dt, bc)
     M = MAT["rho"] * spec.edge ** 3
+    # at t = 0 the body was at rest before: the acceleration of the velocity kink is half the slope
+    np.testing.assert_allclose(o.energy()[1][6:9], 0.5 * M * v / bc.ramp_time, rtol=1e-9)
     for n in (1, 57, n_ramp - 1):
         o.step(n - o.get_state()[3])
         _, R = o.energy()
@@ -343,3 +345,51 @@ def test_kinetic_energy_counts_rotations():
     o.set_state(np.zeros((2, 6)), v, np.zeros((1, 5)))
     (_, _, Wkin, _), _ = o.energy()
     np.testing.assert_allclose(Wkin, 0.5 * (I[0] * v[0, 3:] ** 2).sum() + 0.5 * 1e-6 * 9.0, rtol=1e-14)
+
+
+def test_external_force_with_initial_velocity_balances_energy():
+    """Free pair with initial velocity v0 and constant forces f along it: the supplied energy is the
+    external work plus the initial kinetic energy, so the balance of Sec. 4 holds to rounding
+    (W_ext + W_kin0 = W_kin, no strain)."""
+    m, dt, n = 1e-6, 1e-7, 80
+    spec = two_particle(3.0)
+    bc = workloads.free_bc(2)
+    bc.v0[:, :3] = [5.0, 1.0, -2.0]
+    f = np.zeros((2, 6))
+    f[:, :3] = [0.5, 0.2, 0.1]
+    o = oracle.Oracle(spec, MAT, dt, bc, mass=np.full(2, m), inertia=np.full((2, 3), 1e-7), f_ext=f)
+    o.step(n)
+    (Wext, Wint, Wkin, err), _ = o.energy()
+    Wk0 = 0.5 * m * 2 * float(bc.v0[0, :3] @ bc.v0[0, :3])
+    assert Wint == 0.0 and Wext > 0.1 * Wk0
+    np.testing.assert_allclose(Wkin, Wext + Wk0, rtol=1e-12)
+    assert err < 1e-9
+
+
+def test_divergence_is_reported():
+    """Above the stability limit (dt = 3 dt_c) the explicit step diverges; the oracle reports it
+    (FloatingPointError) from a plain run and from the derivative run alike."""
+    spec = specimen.make_cube_specimen(8.0, 2.0, 4.0, 60, seed=1)
+    bc = workloads.free_bc(spec.n_particles)
+    bc.v0 = np.random.default_rng(0).standard_normal((spec.n_particles, 6))
+    dt_c = oracle.Oracle(spec, EL, 1e-7, bc).critical_dt()
+    o = oracle.Oracle(spec, EL, 3.0 * dt_c, bc)
+    with pytest.raises(FloatingPointError):
+        o.step(3000)
+    o = oracle.Oracle(spec, EL, 3.0 * dt_c, bc)
+    with pytest.raises(FloatingPointError):
+        o.tangent(3000, np.zeros((spec.n_particles, 6)))
+
+
+def test_constrained_dofs_start_at_their_constrained_velocity():
+    """Whatever v0 says, fixed DOFs start at rest and prescribed ones at bc_vel ramp(0)."""
+    spec = two_particle(3.0)
+    bc = workloads.free_bc(2)
+    bc.v0[:, :] = 3.0
+    bc.mask[0, :] = workloads.FIXED
+    bc.mask[1, 0] = workloads.PRESCRIBED
+    bc.vel[1, 0] = 7.0
+    bc.ramp_time = 0.0
+    o = oracle.Oracle(spec, EL, 1e-7, bc, mass=np.full(2, 1e-6), inertia=np.full((2, 3), 1e-7))
+    v = o.get_state()[1]
+    assert np.all(v[0] == 0.0) and v[1, 0] == 7.0 and np.all(v[1, 1:] == 3.0)

@@ -260,3 +260,8 @@ def test_vanishing_tensile_strain_is_elastic_not_nan(eN):
     t, em = oracle.facet_law(MAT, L_EDGE, e, e, 0.0, np.zeros(3), 0.0)
     assert np.all(np.isfinite(t)) and t[0] == MAT["E0"] * eN
     assert em == math.sqrt(eN * eN)  # e_max takes the (vanishing) effective strain, |e_N| here
+    # with shear strains of the same size the response is t = E0 diag(1, alpha, alpha) e
+    e = np.array([eN, eN, -eN])
+    t, _ = oracle.facet_law(MAT, L_EDGE, e, e, 0.0, np.zeros(3), 0.0)
+    E = MAT["E0"] * np.array([1.0, MAT["alpha"], MAT["alpha"]])
+    np.testing.assert_array_equal(t, E * e)
