@@ -332,6 +332,9 @@ def test_energy_balance_restarts_at_set_state():
     (Wext, Wint, Wkin, err), _ = o.energy()
     assert Wext == 0.0 and Wint > 0.05 * Wkin
     assert abs(Wkin + Wint - Wk0) < 1e-2 * Wk0 and err < 1.0
+    # the error of Sec. 4 with the initial kinetic energy as the supplied energy (W_ext = 0 here)
+    assert err > 0.0
+    np.testing.assert_allclose(err, 100.0 * abs(Wk0 - Wint - Wkin) / Wk0, rtol=1e-9)
 
 
 def test_kinetic_energy_counts_rotations():

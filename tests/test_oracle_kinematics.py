@@ -230,3 +230,22 @@ def test_state_exchange_tangential_traction_in_world_frame():
     np.testing.assert_allclose(F3[0], F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
     np.testing.assert_allclose(f6[0, :3], F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
     np.testing.assert_allclose(f6[1, :3], -F, rtol=1e-12, atol=1e-14 * np.abs(F).max())
+
+
+def test_volumetric_strain_per_tetrahedron_under_a_random_field(cube):
+    """e_V of each tetrahedron is (1/3) tr of the gradient of the linear interpolant of the nodal
+    displacements (App. A.2, linearised).  Independent route: solve D^T G = [u_i - u_0] for the
+    gradient G of every tetrahedron (D = vertex offsets), under a random nodal field."""
+    spec, o = cube
+    rng = np.random.default_rng(11)
+    q = np.zeros((spec.n_particles, 6))
+    q[:, :3] = rng.standard_normal((spec.n_particles, 3)) * 1e-3
+    o.set_state(q, np.zeros((spec.n_particles, 6)), np.zeros((spec.n_facets, 5)))
+    _, eV = o.metrics()
+    X, U = spec.x[spec.tets], q[spec.tets, :3]  # [T][4][3]
+    D = X[:, 1:, :] - X[:, :1, :]
+    dU = U[:, 1:, :] - U[:, :1, :]
+    G = np.linalg.solve(D, dU)  # rows of D times G = dU: G[a, b] = d u_b / d x_a
+    expect = np.trace(G, axis1=1, axis2=2) / 3.0
+    assert np.std(expect) > 0.05 * np.abs(expect).max()  # the field is far from uniform
+    np.testing.assert_allclose(eV, expect, rtol=1e-9, atol=1e-12 * np.abs(expect).max())
