@@ -13,6 +13,8 @@ that moves outside its surface).  The checks use no formula of the law itself:
     cap starts at sigma_s with slope mu0 and is concave);
   - every output is finite.
 The material variants of App. A (k_t, E_d, r_s) are included."""
+import zlib
+
 import numpy as np
 import pytest
 
@@ -53,7 +55,7 @@ def _work(t, path):
 def test_closed_cycles_dissipate_and_stay_admissible(variant):
     mat = dict(MAT, **VARIANTS[variant])
     e0 = mat["sigma_t"] / mat["E0"]
-    rng = np.random.default_rng(hash(variant) % (2 ** 32))
+    rng = np.random.default_rng(zlib.crc32(variant.encode()))  # stable across processes, unlike hash()
     dissipated = 0
     for trial in range(12):
         scale = [0.5, 3.0, 12.0][trial % 3]

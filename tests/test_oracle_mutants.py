@@ -14,7 +14,7 @@ def test_every_mutation_site_occurs_exactly_once():
 
 def test_runner_catches_a_total_strain_friction_trial():
     """The friction trial taken from the total strain instead of the increment (App. A.3) passes every
-    closed-form pin of the law and is caught by the incremental-unloading invariant."""
+    closed-form pin of the law; the law invariants catch it."""
     caught, first = om.run_one("shear_total_not_incremental")
     assert caught, first
-    assert "test_friction_unloads_elastically_from_the_cap" in first, first
+    assert "tests/test_oracle_invariants.py::" in first, first
