@@ -58,6 +58,44 @@ def library_path() -> str:
     return _build.LIB
 
 
+def signatures():
+    """ctypes argument and result types of every entry point of include/ldpm.h (pointers and arrays
+    as c_void_p)."""
+    P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    return {
+        "ldpm_create": ([P, P, P, P], C.c_int),
+        "ldpm_step": ([P, I64], C.c_int),
+        "ldpm_sync": ([P], C.c_int),
+        "ldpm_get_state": ([P, P, P, P, P], C.c_int),
+        "ldpm_set_state": ([P, P, P, P, I64], C.c_int),
+        "ldpm_energy": ([P, P, P], C.c_int),
+        "ldpm_facet_forces": ([P, P, P], C.c_int),
+        "ldpm_set_bc": ([P, P, P, D], C.c_int),
+        "ldpm_metrics": ([P, P, P], C.c_int),
+        "ldpm_info": ([P, P, P], C.c_int),
+        "ldpm_profile": ([P, I32], C.c_int),
+        "ldpm_profile_read": ([P, P, P, I32], C.c_int),
+        "ldpm_checkpoint_size": ([P], I64),
+        "ldpm_save_checkpoint": ([P, P], C.c_int),
+        "ldpm_load_checkpoint": ([P, P], C.c_int),
+        "ldpm_destroy": ([P], None),
+        "ldpm_last_error": ([], C.c_char_p),
+        "ldpm_kinetic_energy_noalloc": ([P, P, I64, P, P], C.c_int),
+        "ldpm_batch_create": ([I32, P, P, P, P], C.c_int),
+        "ldpm_batch_step": ([P, I64], C.c_int),
+        "ldpm_batch_size": ([P], I32),
+        "ldpm_batch_get_state": ([P, I32, P, P, P, P], C.c_int),
+        "ldpm_batch_energy": ([P, I32, P, P], C.c_int),
+        "ldpm_batch_metrics": ([P, I32, P, P], C.c_int),
+        "ldpm_batch_info": ([P, I32, P, P], C.c_int),
+        "ldpm_launch_shape": ([P, P], C.c_int),
+        "ldpm_set_facet_params": ([P, P, P, P], C.c_int),
+        "ldpm_perturb": ([P, P], C.c_int),
+        "ldpm_adjoint": ([P, I64, I32, P, P, P, P, P], C.c_int),
+        "ldpm_facet_law_vjp": ([I32, P, I64, P, P, P, P], C.c_int),
+    }
+
+
 def lib():
     """Load libldpm.so (building it first if the sources are newer).  Raises if that fails."""
     global _lib
@@ -67,39 +105,7 @@ def lib():
         if not os.path.exists(path):
             raise ImportError("libldpm.so is missing at %s" % path)
         L = C.CDLL(path)
-        P, I32, I64, D = C.c_void_p, C.c_int32, C.c_int64, C.c_double
-        sig = {
-            "ldpm_create": ([P, P, P, P], C.c_int),
-            "ldpm_step": ([P, I64], C.c_int),
-            "ldpm_sync": ([P], C.c_int),
-            "ldpm_get_state": ([P, P, P, P, P], C.c_int),
-            "ldpm_set_state": ([P, P, P, P, I64], C.c_int),
-            "ldpm_energy": ([P, P, P], C.c_int),
-            "ldpm_facet_forces": ([P, P, P], C.c_int),
-            "ldpm_set_bc": ([P, P, P, D], C.c_int),
-            "ldpm_metrics": ([P, P, P], C.c_int),
-            "ldpm_info": ([P, P, P], C.c_int),
-            "ldpm_profile": ([P, I32], C.c_int),
-            "ldpm_profile_read": ([P, P, P, I32], C.c_int),
-            "ldpm_checkpoint_size": ([P], I64),
-            "ldpm_save_checkpoint": ([P, P], C.c_int),
-            "ldpm_load_checkpoint": ([P, P], C.c_int),
-            "ldpm_destroy": ([P], None),
-            "ldpm_last_error": ([], C.c_char_p),
-            "ldpm_kinetic_energy_noalloc": ([P, P, I64, P, P], C.c_int),
-            "ldpm_batch_create": ([I32, P, P, P, P], C.c_int),
-            "ldpm_batch_step": ([P, I64], C.c_int),
-            "ldpm_batch_size": ([P], I32),
-            "ldpm_batch_get_state": ([P, I32, P, P, P, P], C.c_int),
-            "ldpm_batch_energy": ([P, I32, P, P], C.c_int),
-            "ldpm_batch_metrics": ([P, I32, P, P], C.c_int),
-            "ldpm_batch_info": ([P, I32, P, P], C.c_int),
-            "ldpm_launch_shape": ([P, P], C.c_int),
-            "ldpm_set_facet_params": ([P, P, P, P], C.c_int),
-            "ldpm_perturb": ([P, P], C.c_int),
-            "ldpm_adjoint": ([P, I64, I32, P, P, P, P, P], C.c_int),
-            "ldpm_facet_law_vjp": ([I32, P, I64, P, P, P, P], C.c_int),
-        }
+        sig = signatures()
         for name, (args, res) in sig.items():
             fn = getattr(L, name)
             fn.argtypes = args

@@ -118,3 +118,43 @@ def test_no_cpu_fallback_in_product_path():
     for fn in ("ldpm.py", "__init__.py", "build.py", "specimen.py", "workloads.py", "autograd.py"):
         src = open(os.path.join(ROOT, "paper_2603_13190_gb300", fn)).read()
         assert not re.search(r"^\s*(import|from)\s+oracle", src, re.M), fn
+
+
+def declared_prototypes():
+    """{name: (return type, [parameter types])} of the header's ldpm_* functions, comments removed."""
+    src = ""
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src += open(os.path.join(ROOT, "include", fn)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"^\s*((?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**)\s*(ldpm_[a-z0-9_]+)\s*\(([^;{]*?)\)\s*;",
+                                        src, re.M | re.S):
+        ps = [p.strip() for p in params.replace("\n", " ").split(",") if p.strip() and p.strip() != "void"]
+        out[name] = (ret.strip(), ps)
+    return out
+
+
+def _ctype_of(decl: str):
+    import ctypes as C
+
+    if "*" in decl or "[" in decl or decl.split()[0] == "ldpm_t":
+        return C.c_void_p
+    base = decl.replace("const ", "").split()[0]
+    return {"int32_t": C.c_int32, "int64_t": C.c_int64, "double": C.c_double, "int": C.c_int}[base]
+
+
+def test_binding_signatures_match_the_header():
+    """The ctypes table of the binding agrees with every prototype of include/ldpm.h, argument by
+    argument (a drift here would pass wrong-width values across the ABI)."""
+    import ctypes as C
+
+    protos = declared_prototypes()
+    sig = ldpm.signatures()
+    assert sorted(protos) == sorted(sig)
+    rets = {"int": C.c_int, "int64_t": C.c_int64, "int32_t": C.c_int32, "void": None, "const char *": C.c_char_p,
+            "const char*": C.c_char_p}
+    for name, (ret, params) in protos.items():
+        args, res = sig[name]
+        assert [_ctype_of(p) for p in params] == list(args), (name, params, args)
+        assert rets[" ".join(ret.split())] == res, (name, ret, res)
