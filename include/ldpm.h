@@ -74,7 +74,9 @@ typedef struct {
                                  nodes with d = 0 take the smallest positive diameter */
 } ldpm_geometry;
 
-/* Material parameters, Appendix A table (names follow the paper's symbols). */
+/* Material parameters, Appendix A table (names follow the paper's symbols).  ldpm_create checks
+ * (LDPM_E_INVALID_ARG otherwise): every value finite; rho, E0, alpha, sigma_t, l_t, r_st, sigma_c0,
+ * kc3, sigma_N0, Ed_E0 > 0; n_t, k_t, r_s >= 0; kc0 >= 1; reserved == 0. */
 typedef struct {
     double rho;      /* density */
     double E0;       /* effective normal modulus */
@@ -89,10 +91,11 @@ typedef struct {
     double kc0, kc1, kc2, kc3; /* kappa_c0..kappa_c3 */
     double mu0, mu_inf;        /* initial and asymptotic friction */
     double sigma_N0;           /* transitional stress */
-    double Ed_E0;              /* densification ratio (only 1 is supported) */
+    double Ed_E0;              /* E_d / E0: normal stiffness while -t_N exceeds sigma_c0 (App. A.2) */
     double beta;               /* volumetric-deviatoric coupling */
-    double k_t;                /* tensile unloading (only 0 is supported) */
-    double r_s;                /* shear softening modulus ratio (only 0 is supported) */
+    double k_t;                /* tensile reload: from zero traction, reloading starts at
+                                  e_tr = k_t (e_max - sigma_bt / E0) (App. A.1); 0 = at once */
+    double r_s;                /* shear softening modulus ratio, H_s = r_s E0 (App. A.1) */
     int32_t elastic;           /* 1: linear elastic facets t = E e (Sec. 2) */
     int32_t reserved;          /* must be 0 */
 } ldpm_material;

@@ -158,3 +158,33 @@ def test_binding_signatures_match_the_header():
         args, res = sig[name]
         assert [_ctype_of(p) for p in params] == list(args), (name, params, args)
         assert rets[" ".join(ret.split())] == res, (name, ret, res)
+
+
+def header_struct(name):
+    """[(field, C type)] of `typedef struct { ... } name;` in include/ldpm.h, comments removed."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ldpm.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct\s*\{([^{}]*)\}\s*%s\s*;" % name, src).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"(?:const\s+)?([A-Za-z_][A-Za-z0-9_]*)\s+(.*)", decl)
+        base, names = m.group(1), m.group(2)
+        for n in names.split(","):
+            n = n.strip()
+            fields.append((n.lstrip("*").strip(), "ptr" if n.startswith("*") or base == "void" else base))
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("ldpm_geometry", "Geometry"), ("ldpm_material", "Material"),
+                                          ("ldpm_options", "Options")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """Field names, order and C types of the ABI structs agree with their ctypes mirrors."""
+    import ctypes as C
+
+    want = {"ptr": C.c_void_p, "int32_t": C.c_int32, "double": C.c_double}
+    got = [(f, t) for f, t in getattr(ldpm, pyname)._fields_]
+    hdr = header_struct(cname)
+    assert [f for f, _ in hdr] == [f for f, _ in got], (cname, hdr, got)
+    assert [want[t] for _, t in hdr] == [t for _, t in got], cname
