@@ -40,7 +40,7 @@ extern "C" {
 #define LDPM_E_OOM (-4)           /* device or host allocation failed */
 #define LDPM_E_UNSTABLE (-5)      /* a velocity or displacement became NaN/Inf (step too large?) */
 #define LDPM_E_TIMEOUT (-6)       /* reserved for a bounded device-side wait; no kernel waits today */
-#define LDPM_E_UNSUPPORTED (-7)   /* a parameter combination the library does not implement */
+#define LDPM_E_UNSUPPORTED (-7)   /* reserved; no call returns it today */
 
 typedef struct ldpm_ctx *ldpm_t; /* opaque handle, owned by the library */
 
@@ -129,8 +129,7 @@ typedef struct {
  * arms and projected areas, the lumped mass, the particle-to-facet CSR list and the Morton-ordered
  * device layout, uploads, and estimates dt if not given.  Initial state: q = 0, v = v0 (fixed DOFs
  * 0, prescribed DOFs at their prescribed velocity), zero facet history.  On success *out owns all
- * device memory.  Errors: INVALID_ARG, BAD_GEOMETRY, UNSUPPORTED (k_t != 0, r_s != 0,
- * Ed_E0 != 1), OOM, CUDA. */
+ * device memory.  Errors: INVALID_ARG (options, material checks), BAD_GEOMETRY, OOM, CUDA. */
 int ldpm_create(const ldpm_geometry *geom, const ldpm_material *mat, const ldpm_options *opt, ldpm_t *out);
 
 /* Enqueue nsteps central-difference steps (Sec. 3) on the handle's stream and return without
@@ -283,7 +282,7 @@ int ldpm_adjoint(ldpm_t h, int64_t nsteps, int32_t ckpt_every, const double *see
  * sigma_t, 0 (the remaining parameters from *mat).  adj_out [n][4] = adjoints of the new t_N, t_M,
  * t_L, e_max.  Writes out [n][4] = new t_N, t_M, t_L, e_max and adj_in [n][16] = the adjoints of the
  * inputs in the layout of `in` (slots 0 and 15 zero).  precision: LDPM_FP64 or LDPM_MIXED (FP32
- * law).  Synchronous; uses the current CUDA device.  Errors: INVALID_ARG, UNSUPPORTED, OOM, CUDA. */
+ * law).  Synchronous; uses the current CUDA device.  Errors: INVALID_ARG, OOM, CUDA. */
 int ldpm_facet_law_vjp(int32_t precision, const ldpm_material *mat, int64_t n, const double *in, const double *adj_out,
                        double *out, double *adj_in);
 
