@@ -188,3 +188,20 @@ def test_binding_structs_match_the_header(cname, pyname):
     hdr = header_struct(cname)
     assert [f for f, _ in hdr] == [f for f, _ in got], (cname, hdr, got)
     assert [want[t] for _, t in hdr] == [t for _, t in got], cname
+
+
+def test_error_codes_documented_as_returned_are_returned():
+    """Every LDPM_E_* code of the header is produced somewhere in the library's sources, except the
+    ones the header marks reserved, which none produces; the binding names every code."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "ldpm.h")).read(), flags=re.S)
+    raw = open(os.path.join(ROOT, "include", "ldpm.h")).read()
+    codes = dict(re.findall(r"#define (LDPM_E_[A-Z_]+) \((-\d+)\)", src))
+    reserved = set(re.findall(r"#define (LDPM_E_[A-Z_]+) \(-\d+\)\s*/\*\s*reserved", raw))
+    csrc = os.path.join(ROOT, "paper_2603_13190_gb300", "csrc")
+    used = set()
+    for f in os.listdir(csrc):
+        used |= set(re.findall(r"LDPM_E_[A-Z_]+", open(os.path.join(csrc, f)).read()))
+    assert reserved <= set(codes)
+    for c in codes:
+        assert (c in used) != (c in reserved), c
+        assert ldpm.ERRORS[int(codes[c])] == c
