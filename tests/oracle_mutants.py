@@ -350,6 +350,31 @@ MUTANTS = [
     ('tN_trial_total',
      'S tN = t_old[0] + ENc * de[0];',
      'S tN = ENc * e[0];'),
+    # branch selection, the L components, strain projection, per-facet parameter slots, outputs
+    ('branch_on_e_N_nonnegative',
+     '    if (e[0] > 0.0) {\n        /* App. A.1, fracture.',
+     '    if (e[0] >= 0.0) {\n        /* App. A.1, fracture.'),
+    ('friction_trial_L_no_alpha',
+     'S tL = t_old[2] + alpha * E0 * de[2];',
+     'S tL = t_old[2] + E0 * de[2];'),
+    ('strain_M_projects_on_n',
+     'e[1] = (m[0] * jump[0] + m[1] * jump[1] + m[2] * jump[2]) / l;',
+     'e[1] = (n[0] * jump[0] + n[1] * jump[1] + n[2] * jump[2]) / l;'),
+    ('strains_output_of_facet_0',
+     'for (int32_t k = 0; k < M->F; ++k) facet_strain(M, q, k, e3 + 3 * (size_t)k);',
+     'for (int32_t k = 0; k < M->F; ++k) facet_strain(M, q, 0, e3 + 3 * (size_t)k);'),
+    ('elastic_operator_L_no_alpha',
+     't[2] = M->mat.alpha * M->mat.E0 * e[2];',
+     't[2] = M->mat.E0 * e[2];'),
+    ('facet_params_alpha_sigma_swapped',
+     'double **dst[3] = {&M->pE0, &M->palpha, &M->psig};',
+     'double **dst[3] = {&M->pE0, &M->psig, &M->palpha};'),
+    ('jacobian_E0_alpha_slots_swapped',
+     'facet_law<S>(p, x[11], x[12], x[13], l, x, x + 3, x[6], x + 7, x[10], tn, &em);',
+     'facet_law<S>(p, x[12], x[11], x[13], l, x, x + 3, x[6], x + 7, x[10], tn, &em);'),
+    ('geometry_area_unreported',
+     'if (area) memcpy(area, M->area, sizeof(double) * M->F);',
+     ';'),
 ]
 
 
