@@ -307,6 +307,117 @@ __device__ __forceinline__ double f2d_bits(float f)
     return __longlong_as_double((long long)(sign | (ed << 52) | ((uint64_t)(u & 0x7fffffu) << 29)));
 }
 
+// ------------------------------------------------------------------------------------------------
+// Compensated ("float-float") arithmetic on the FP32 pipe.  A value is the unevaluated sum hi + lo of
+// two floats (48 mantissa bits).  two_sum is Knuth's error-free addition (TAOCP vol. 2, 4.2.2):
+// s + e == a + b exactly; fast_two_sum is Dekker's (1971) for |a| >= |b|; the product's rounding
+// error is exact with one FMA.  The mixed mode sums forces and energies with these: the GB300 FP64
+// pipe issues one warp instruction per ~64 cycles per sub-partition, the FP32 pipe one per cycle.
+// Every operation is written with explicit round-to-nearest intrinsics so the compiler neither
+// contracts nor reorders them.
+// ------------------------------------------------------------------------------------------------
+struct ff {
+    float hi, lo;
+};
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ff fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+// a += x (x a float): the rounding error of the running sum is collected in a.lo
+__device__ __forceinline__ void ff_acc(ff &a, float x)
+{
+    const ff t = two_sum(a.hi, x);
+    a.hi = t.hi;
+    a.lo = __fadd_rn(a.lo, t.lo);
+}
+// a += x (x a float-float)
+__device__ __forceinline__ void ff_acc(ff &a, ff x)
+{
+    const ff t = two_sum(a.hi, x.hi);
+    a.hi = t.hi;
+    a.lo = __fadd_rn(a.lo, __fadd_rn(t.lo, x.lo));
+}
+__device__ __forceinline__ ff ff_norm(ff a) { return fast_two_sum(a.hi, a.lo); }
+// a + b; absolute error below ~2^-46 (|a| + |b|), the form of an FP64 addition's bound
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = two_sum(a.hi, b.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return fast_two_sum(p, e);
+}
+__device__ __forceinline__ ff ff_shfl_xor(ff a, int off)
+{
+    return {__shfl_xor_sync(0xffffffffu, a.hi, off), __shfl_xor_sync(0xffffffffu, a.lo, off)};
+}
+// FP64 value as a float-float (integer-pipe split; relative error below 2^-46) and back (one FP64
+// addition of two exactly converted floats).
+__device__ __forceinline__ ff ff_from_double(double x)
+{
+    ff r;
+    d2f_split(x, r.hi, r.lo);
+    return r;
+}
+__device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
+
+// Accumulator operations shared by the FP64 sums (double) and the mixed-mode sums (float-float).
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }
+__device__ __forceinline__ double acc_shfl_xor(double a, int off) { return __shfl_xor_sync(0xffffffffu, a, off); }
+__device__ __forceinline__ ff acc_shfl_xor(ff a, int off) { return ff_shfl_xor(a, off); }
+
+// Sum of v[0..5] over each aligned group of 8 lanes, by halving exchanges: at each level a lane keeps
+// half of its values (the upper half when its lane bit is set) and adds its partner's copy of that
+// half (3 + 2 + 1 additions instead of 3 x 6; the second level pads its 3 values with a zero).
+// Afterwards v[0] of lane L (L = lane & 7) holds the group sum of value kHalvingSlot[L]: lanes
+// 0, 1, 2, 4, 5, 6 hold values 0..5, lanes 3 and 7 zero.  The order of the additions is fixed.
+template <class A>
+__device__ __forceinline__ void halving_sum6(A (&v)[6], int lane)
+{
+    A w[4];
+    {
+        const bool upper = (lane & 4) != 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const A keep = upper ? v[3 + i] : v[i];
+            const A give = upper ? v[i] : v[3 + i];
+            w[i] = acc_add(keep, acc_shfl_xor(give, 4));
+        }
+        w[3] = A{};
+    }
+    {
+        const bool upper = (lane & 2) != 0;
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const A keep = upper ? w[2 + i] : w[i];
+            const A give = upper ? w[i] : w[2 + i];
+            w[i] = acc_add(keep, acc_shfl_xor(give, 2));
+        }
+    }
+    {
+        const bool upper = (lane & 1) != 0;
+        const A keep = upper ? w[1] : w[0];
+        const A give = upper ? w[0] : w[1];
+        v[0] = acc_add(keep, acc_shfl_xor(give, 1));
+    }
+}
+// Component held by lane L of an 8-lane group after halving_sum6 (-1: none).
+__device__ __forceinline__ int halving_slot6(int L) { return L < 3 ? L : (L == 3 || L == 7 ? -1 : L - 1); }
+
 // FP32 mirror entries of DOF d of a particle after its FP64 q and v changed.
 __device__ __forceinline__ void write_mirror(float *pm, int d, double q, double v)
 {

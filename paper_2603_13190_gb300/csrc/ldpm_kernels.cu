@@ -459,32 +459,36 @@ __global__ void __launch_bounds__(32 * WPB)
 
 // ------------------------------------------------------------------------------------------------
 // Particle pass.  A group of LPP lanes owns one particle: it sums the particle's (tetrahedron,
-// vertex) contributions in CSR order (Eq. (2a)-(2b)), reduces across the group, and lanes 0..5 of the
-// group update one DOF each.  With LPP = 8 a warp updates 4 particles per instruction.
+// vertex) contributions in CSR order (Eq. (2a)-(2b)), reduces across the group by halving exchanges,
+// after which lanes 0, 1, 2, 4, 5, 6 of the group hold components 0..5 and update one DOF each.  With
+// LPP = 8 a warp updates 4 particles per instruction.
 // The particle's own records (mass, constraint, q, v, f_n) do not depend on the contributions and are
 // loaded before the sum, so their latency overlaps the CSR gather.
-// FP64 mode: everything after the sum is FP64.  Mixed mode: the contributions and their sums are
-// FP32, and so are the energy increments formed from them (their rounding is of the order of the FP32
-// forces'); the velocity and displacement updates are FP64 as in FP64 mode, so the trajectory is the
-// one the FP64 update of the FP32 forces gives.  The energy terms were the larger part of the FP64
-// instructions: the GB300 FP64 pipe issues one warp instruction per ~64 cycles per sub-partition.
-// The FP32 <-> FP64 conversions are integer operations.
+// FP64 mode: everything is FP64.  Mixed mode: the shares are FP32 (each the sum of a tetrahedron's 6
+// FP32 facet terms at one vertex); the particle sums of the shares are float-float (48 mantissa bits),
+// converted to FP64 once; the velocity and displacement updates are FP64 as in FP64 mode; the energy
+// increments (trapezoid products and their 6-DOF sums) are float-float, added into the FP64
+// accumulators.  The GB300 FP64 pipe issues one warp instruction per
+// ~64 cycles per sub-partition, so the compensated sums run on the FP32 pipe; FP32 <-> FP64
+// conversions are integer operations.
 // ------------------------------------------------------------------------------------------------
 template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
     static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per particle");
-    using R2 = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
     constexpr bool kMixed = sizeof(R) == 4;
+    using Acc = typename std::conditional<kMixed, ff, double>::type;
     const int32_t *__restrict__ ent = static_cast<const int32_t *>(m.ent);
     const R *__restrict__ tvc = static_cast<const R *>(m.tvc);
     const int lane = threadIdx.x & 31;
     const int sub = lane & (LPP - 1);
     const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
     const bool valid = p < m.N;
-    // lanes 0..5 of the group own one DOF each; the other lanes mirror DOF 0 and store nothing
-    const bool act = valid && sub < 6;
-    const int d = sub < 6 ? sub : 0;
+    // lanes 0, 1, 2, 4, 5, 6 of the group own DOFs 0..5 (where halving_sum6 leaves their sums); the
+    // other lanes mirror DOF 0 and store nothing
+    const int slot6 = sub < 8 ? halving_slot6(sub) : -1;
+    const bool act = valid && slot6 >= 0;
+    const int d = slot6 >= 0 ? slot6 : 0;
     const int64_t pc_ = valid ? p : 0;
     int r0 = 0, r1 = 0;
     if (valid) {
@@ -504,46 +508,71 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) gather_kernel(Dev
         sp = (int)__double_as_longlong(pc[7]);
         vh = ps[9 + d];
         q0 = ps[3 + d];
-        fa_old = pd[d];
         if (has_fext) fe = m.f_ext[6 * pc_ + d];
     }
     // each entry is one (tetrahedron, vertex) slot: 6 values, force (3) and moment about the particle (3)
     // kSlots entries per lane in flight
     constexpr int kSlots = 2;
-    R a[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+    Acc a[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = Acc{};
     for (int r = r0 + sub; r < r1; r += kSlots * LPP) {
         int id[kSlots];
 #pragma unroll
         for (int k = 0; k < kSlots; ++k) id[k] = (r + k * LPP < r1) ? ent[r + k * LPP] : -1;
-        R2 w[kSlots][3];
+        if constexpr (kMixed) {
+            float2 w[kSlots][3];
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k)
-            if (id[k] >= 0) {
-                const R2 *src = reinterpret_cast<const R2 *>(tvc + 6 * (int64_t)id[k]);
-                w[k][0] = src[0];
-                w[k][1] = src[1];
-                w[k][2] = src[2];
-            }
+            for (int k = 0; k < kSlots; ++k)
+                if (id[k] >= 0) {
+                    const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)id[k]);
+                    w[k][0] = src[0];
+                    w[k][1] = src[1];
+                    w[k][2] = src[2];
+                }
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k)
-            if (id[k] >= 0) {
-                a[0] += w[k][0].x;
-                a[1] += w[k][0].y;
-                a[2] += w[k][1].x;
-                a[3] += w[k][1].y;
-                a[4] += w[k][2].x;
-                a[5] += w[k][2].y;
-            }
+            for (int k = 0; k < kSlots; ++k)
+                if (id[k] >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        ff_acc(a[2 * c], w[k][c].x);
+                        ff_acc(a[2 * c + 1], w[k][c].y);
+                    }
+                }
+        } else {
+            double2 w[kSlots][3];
+#pragma unroll
+            for (int k = 0; k < kSlots; ++k)
+                if (id[k] >= 0) {
+                    const double2 *src = reinterpret_cast<const double2 *>(tvc + 6 * (int64_t)id[k]);
+                    w[k][0] = src[0];
+                    w[k][1] = src[1];
+                    w[k][2] = src[2];
+                }
+#pragma unroll
+            for (int k = 0; k < kSlots; ++k)
+                if (id[k] >= 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        a[2 * c] += w[k][c].x;
+                        a[2 * c + 1] += w[k][c].y;
+                    }
+                }
+        }
     }
+    // lanes beyond the first 8 of a group fold into them, then the halving sum leaves component
+    // halving_slot6(sub & 7) of the particle's total in a[0]
 #pragma unroll
-    for (int off = LPP / 2; off > 0; off >>= 1)
+    for (int off = LPP / 2; off >= 8; off >>= 1)
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
-    R fr = a[0];
-#pragma unroll
-    for (int k = 1; k < 6; ++k)
-        if (d == k) fr = a[k];
-    const double fa_new = to_double<R>(fr);
+        for (int k = 0; k < 6; ++k) a[k] = acc_add(a[k], acc_shfl_xor(a[k], off));
+    if (MODE != GATHER_ASSEMBLE) fa_old = pd[d];  // f_n: needed only by the energy increments
+    halving_sum6(a, lane);
+    double fa_new;
+    if constexpr (kMixed)
+        fa_new = ff_to_double(ff_norm(a[0]));
+    else
+        fa_new = a[0];
     if (MODE == GATHER_ASSEMBLE) {
         if (act) out6[6 * p + d] = fa_new;
         return;
@@ -564,53 +593,51 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 6 : 1) gather_kernel(Dev
         v_bc = m.bc_vel[6 * pc_ + d] * r_next;
     }
     double v_next, dWi_acc, dWe_acc;
+    if (mask == 0) {
+        const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
+        v_next = (vh + dv) + dv;
+    } else {
+        v_next = mask == 1 ? 0.0 : v_bc;
+    }
+    // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2},
+    //   dW_int = -(f_n + f_{n+1}) dq / 2 on every DOF, dW_ext = g dq / 2 with g the sum of the
+    //   external forces (2 f_ext on loaded DOFs, the supports' reactions on constrained ones)
     if constexpr (kMixed) {
-        const float f = fr;
-        const float fo = d2f_trunc(fa_old);  // exact: f_n was stored from an FP32 sum
-        const float hdt_f = d2f_rn(hdt);
-        float g = 0.0f;
+        const ff fsum = ff_add(ff_from_double(fa_old), ff_from_double(fa_new));
+        const ff hdq = ff_mul(ff_from_double(hdt), ff_from_double(vh));
+        ff g = {0.0f, 0.0f};
         if (mask == 0) {
-            const float fe_f = has_fext ? d2f_rn(fe) : 0.0f;
-            const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
-            if (has_fext) g = 2.0f * fe_f;
-            v_next = (vh + dv) + dv;
-        } else if (mask == 1) {
-            g = -(fo + f);
-            v_next = 0.0;
+            if (has_fext) {
+                const ff f1 = ff_from_double(fe);
+                g = ff{2.0f * f1.hi, 2.0f * f1.lo};
+            }
         } else {
-            g = d2f_rn(g_bc) - (fo + f);
-            v_next = v_bc;
+            g = mask == 1 ? ff_neg(fsum) : ff_add(ff_from_double(g_bc), ff_neg(fsum));
         }
-        // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
-        const float hdq = hdt_f * d2f_rn(vh);
-        float dWi = act ? -(fo + f) * hdq : 0.0f;
-        float dWe = (need_we && act) ? g * hdq : 0.0f;
+        ff dWi = act ? ff_neg(ff_mul(fsum, hdq)) : ff{0.0f, 0.0f};
+        ff dWe = (need_we && act) ? ff_mul(g, hdq) : ff{0.0f, 0.0f};
+        // sum the six DOF contributions into lane 0 of the group (lanes 3, 7 hold zeros)
 #pragma unroll
-        for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
+        for (int off = 4; off > 0; off >>= 1) dWi = ff_add(dWi, ff_shfl_xor(dWi, off));
         if (need_we) {
 #pragma unroll
-            for (int off = 4; off > 0; off >>= 1) dWe += __shfl_xor_sync(0xffffffffu, dWe, off);
+            for (int off = 4; off > 0; off >>= 1) dWe = ff_add(dWe, ff_shfl_xor(dWe, off));
         }
-        dWi_acc = f2d_bits(dWi);
-        dWe_acc = f2d_bits(dWe);
+        dWi_acc = ff_to_double(dWi);
+        dWe_acc = need_we ? ff_to_double(dWe) : 0.0;
     } else {
         double g_sum = 0.0;
         if (mask == 0) {
-            const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
             if (has_fext) g_sum = 2.0 * fe;
-            v_next = (vh + dv) + dv;
         } else if (mask == 1) {
             g_sum = -(fa_old + fa_new);
-            v_next = 0.0;
         } else {
             g_sum = g_bc - (fa_old + fa_new);
-            v_next = v_bc;
         }
-        // energy increments over [t_n, t_{n+1}] (trapezoid): dq = dt v_{n+1/2}
         const double hdq = hdt * vh;
         double dWi = act ? -(fa_old + fa_new) * hdq : 0.0;
         double dWe = (need_we && act) ? g_sum * hdq : 0.0;
-        // sum the six DOF contributions into lane 0 of the group (lanes 6, 7 hold zeros)
+        // sum the six DOF contributions into lane 0 of the group (lanes 3, 7 hold zeros)
 #pragma unroll
         for (int off = 4; off > 0; off >>= 1) dWi += __shfl_xor_sync(0xffffffffu, dWi, off);
         if (need_we) {
