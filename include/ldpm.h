@@ -155,6 +155,18 @@ int ldpm_sync(ldpm_t h);
  * until ldpm_destroy (OOM if it cannot). */
 int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step);
 
+/* The state of ldpm_get_state (Sec. 2: particle displacements and rotations q, velocities v, facet
+ * tractions and e_max; Sec. 3: whole-step values q_n, v_n), written into caller-owned DEVICE buffers
+ * on the handle's device: q, v [N][6] FP64 in caller particle order, hist5 [F][5] FP64 in caller facet
+ * order (the layout of ldpm_get_state), step one int64.  Any pointer may be NULL.  A batch handle
+ * writes all specimens concatenated in index order.  The conversion runs in kernels enqueued on the
+ * handle's stream; the call returns without waiting and without any host copy, so a caller on
+ * another stream orders its use of the buffers after the handle's stream (a torch caller passes its
+ * stream at create, or waits on an event).  Allocates nothing.  It does not report a non-finite
+ * state (ldpm_sync does).  Errors: INVALID_ARG (bad handle), CUDA (a launch failed, e.g. a buffer on
+ * another device). */
+int ldpm_get_state_device(ldpm_t h, double *q, double *v, double *hist5, int64_t *step);
+
 /* Replace the state (synchronises).  Same layouts as ldpm_get_state; hist5 may be NULL (zero
  * history).  The internal forces of the new state are rebuilt from the given tractions; energy
  * accumulators restart (W_ext = W_int = 0, W_kin0 = kinetic energy of v). */
@@ -210,7 +222,10 @@ int ldpm_load_checkpoint(ldpm_t h, const void *buf);
  * block of 1024 DOFs) is a 32 KiB static device array that every GPU loading the library holds until
  * exit, so n_dof is limited to 4,194,304 (LDPM_E_INVALID_ARG beyond it, nothing launched).  The first
  * call on a device looks up that array's device address (cudaGetSymbolAddress) with the device
- * current; make that first call before any stream capture.  All calls share the one array: every
+ * current; make that first call before any stream capture.  The address is kept per device ordinal
+ * for the life of the process and belongs to the device's primary context: after cudaDeviceReset of
+ * that device, or when the caller makes a non-primary (driver API) context current, it is no longer
+ * valid, so call this function only from the primary context and not after a reset.  All calls share the one array: every
  * call overwrites the partials it reads, so nothing needs clearing, but calls that overlap on the GPU
  * (on different streams, or from different threads) race on it and must be serialised by the
  * caller.  The result equals the W_kin of ldpm_energy for the same velocities and masses up to

@@ -212,6 +212,7 @@ struct ldpm_ctx {
     double *d_partial = nullptr, *d_out16 = nullptr, *h_out16 = nullptr;
     unsigned *d_ticket = nullptr;       // block counter of the energy reduction
     int32_t *d_umap = nullptr;          // caller's facets of all specimens, concatenated: 2 f + orientation flip
+    int32_t *d_pmap = nullptr;          // caller's particles of all specimens, concatenated: internal particle
     std::vector<int64_t> ufoff;         // [n_spec + 1] offsets of each specimen's facets in d_umap
     double *d_scratch = nullptr;        // state read-back scratch, grown on demand
     size_t scratch_n = 0;
@@ -235,7 +236,8 @@ void free_model(ldpm_ctx *h)
                     h->dm.tet,
                     h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
-                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch, h->d_ticket};
+                    h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch, h->d_ticket,
+                    h->d_pmap};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_out16) cudaFreeHost(h->h_out16);
@@ -930,8 +932,17 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
         (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())) ||
-        (rc = dalloc(&h->d_ticket, 1)))
+        (rc = dalloc(&h->d_ticket, 1)) || (rc = dalloc(&h->d_pmap, (size_t)N)))
         return rc;
+    {
+        std::vector<int32_t> pmap((size_t)N);
+        size_t base = 0;
+        for (const SpecHost &S : h->sp) {
+            for (int32_t i = 0; i < S.N; ++i) pmap[base + i] = S.p0 + S.inv_p[i];
+            base += S.N;
+        }
+        CU(cudaMemcpy(h->d_pmap, pmap.data(), pmap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     CU(cudaMemset(h->d_ticket, 0, sizeof(unsigned)));
     CU(cudaMemcpy(h->d_umap, umap.data(), umap.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     if (H.any_fext) {
@@ -1434,6 +1445,21 @@ int ldpm_get_state(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
     g_err.clear();
     if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
     return get_state_range(h, 0, (int)h->sp.size(), q, v, hist5, step);
+}
+
+int ldpm_get_state_device(ldpm_t h, double *q, double *v, double *hist5, int64_t *step)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    DevGuard dg(h->device);
+    CU(launch_state_to_user(h->dm, h->d_pmap, h->dm.N, q, v, h->stream));
+    if (hist5) {
+        const int64_t nf = h->ufoff.back();
+        CU(h->prec == LDPM_MIXED ? launch_hist_to_user<float>(h->dm, h->d_umap, nf, hist5, h->stream)
+                                 : launch_hist_to_user<double>(h->dm, h->d_umap, nf, hist5, h->stream));
+    }
+    if (step) CU(cudaMemcpyAsync(step, h->dm.step, sizeof(int64_t), cudaMemcpyDeviceToDevice, h->stream));
+    return LDPM_OK;
 }
 
 int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *hist5, int64_t step)

@@ -128,6 +128,10 @@ void set_last_error(const char *msg);
 cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s);
 // unkick: the inverse; into out12 [N][12] (q_n then v_n) or, with out12 null, in place.
 cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s);
+// Whole-step state in the caller's particle order: caller particle k is internal particle pmap[k];
+// q, v [n][6] device arrays (either may be null).
+cudaError_t launch_state_to_user(const DeviceModel &m, const int32_t *pmap, int64_t n, double *q, double *v,
+                                 cudaStream_t s);
 // `src_override` replaces the particle records the facet pass reads (FP64 mode: pstate layout;
 // mixed mode: pm32 layout); null = the model's own.
 template <class R>

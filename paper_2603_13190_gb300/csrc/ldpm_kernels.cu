@@ -690,21 +690,16 @@ __global__ void __launch_bounds__(256) kick_kernel(DeviceModel m)
     if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, q, vh);
 }
 
-// Whole-step state (q_n, v_n) from the drifted state (q_{n+1}, v_{n+1/2}) the library keeps between
-// calls: the inverse of kick_kernel under the same boundary conditions.  out12 [N][12] (q then v),
-// or null to rewrite pstate (and the mirror) in place.
-__global__ void __launch_bounds__(256) unkick_kernel(DeviceModel m, double *__restrict__ out12)
+// Whole-step values (q_n, v_n) of DOF d of internal particle p from the drifted state (q_{n+1},
+// v_{n+1/2}) the library keeps between calls: the inverse of kick_kernel under the same boundary
+// conditions.
+__device__ __forceinline__ void unkick_dof(const DeviceModel &m, int64_t p, int d, double &qn, double &vn)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 6 * (int64_t)m.N) return;
-    const int64_t p = i / 6;
-    const int d = (int)(i - 6 * p);
-    double *ps = m.pstate + 16 * p;
+    const double *ps = m.pstate + 16 * p;
     const double *pc = m.pconst + 8 * p;
     const int mask = (int)(((uint64_t)__double_as_longlong(pc[6]) >> (8 * d)) & 0xffu);
     const SpecDyn &S = m.spec[(int)__double_as_longlong(pc[7])];
     const double vh = ps[9 + d];
-    double vn;
     if (mask == 0) {
         const double fe = m.f_ext ? m.f_ext[6 * p + d] : 0.0;
         vn = vh - S.half_dt * (fe + m.pdyn[8 * p + d]) * pc[d];
@@ -713,15 +708,43 @@ __global__ void __launch_bounds__(256) unkick_kernel(DeviceModel m, double *__re
     } else {
         vn = m.bc_vel[6 * p + d] * ramp((double)(*m.step) * S.dt, S.inv_ramp);
     }
-    const double qn = ps[3 + d] - S.dt * vh;
+    qn = ps[3 + d] - S.dt * vh;
+}
+
+// Whole-step state into out12 [N][12] (q then v, internal order), or with out12 null into pstate (and
+// the mirror) in place.
+__global__ void __launch_bounds__(256) unkick_kernel(DeviceModel m, double *__restrict__ out12)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * (int64_t)m.N) return;
+    const int64_t p = i / 6;
+    const int d = (int)(i - 6 * p);
+    double qn, vn;
+    unkick_dof(m, p, d, qn, vn);
     if (out12) {
         out12[12 * p + d] = qn;
         out12[12 * p + 6 + d] = vn;
     } else {
+        double *ps = m.pstate + 16 * p;
         ps[3 + d] = qn;
         ps[9 + d] = vn;
         if (m.pm32) write_mirror(m.pm32 + kMirror * p, d, qn, vn);
     }
+}
+
+// Whole-step state in the caller's particle order: caller particle k is internal particle pmap[k];
+// q, v [n][6] (either may be null).
+__global__ void __launch_bounds__(256) state_to_user_kernel(DeviceModel m, const int32_t *__restrict__ pmap, int64_t n,
+                                                            double *__restrict__ q, double *__restrict__ v)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 6 * n) return;
+    const int64_t k = i / 6;
+    const int d = (int)(i - 6 * k);
+    double qn, vn;
+    unkick_dof(m, pmap[k], d, qn, vn);
+    if (q) q[i] = qn;
+    if (v) v[i] = vn;
 }
 
 // FP32 mirror of every particle from the FP64 records.
@@ -961,6 +984,14 @@ cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s)
     const int64_t n = 6 * (int64_t)m.N;
     if (n == 0) return cudaSuccess;
     unkick_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(m, out12);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_state_to_user(const DeviceModel &m, const int32_t *pmap, int64_t n, double *q, double *v,
+                                 cudaStream_t s)
+{
+    if (n <= 0 || (!q && !v)) return cudaSuccess;
+    state_to_user_kernel<<<(unsigned)((6 * n + 255) / 256), 256, 0, s>>>(m, pmap, n, q, v);
     return cudaGetLastError();
 }
 

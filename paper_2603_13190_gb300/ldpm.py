@@ -67,6 +67,7 @@ def signatures():
         "ldpm_step": ([P, I64], C.c_int),
         "ldpm_sync": ([P], C.c_int),
         "ldpm_get_state": ([P, P, P, P, P], C.c_int),
+        "ldpm_get_state_device": ([P, P, P, P, P], C.c_int),
         "ldpm_set_state": ([P, P, P, P, I64], C.c_int),
         "ldpm_energy": ([P, P, P], C.c_int),
         "ldpm_facet_forces": ([P, P, P], C.c_int),
@@ -259,6 +260,12 @@ def ldpm_get_state(h, N: int, F: int, hist: bool = True):
     return q, v, h5, st.value
 
 
+def ldpm_get_state_device(h, q_dev: int, v_dev: int, hist5_dev: int, step_dev: int) -> None:
+    """Device addresses (ints, 0 = NULL) of caller-owned buffers on the handle's device."""
+    _check(lib().ldpm_get_state_device(h, q_dev or None, v_dev or None, hist5_dev or None, step_dev or None),
+           "ldpm_get_state_device")
+
+
 def ldpm_set_state(h, q, v, hist5=None, step: int = 0) -> None:
     q = np.ascontiguousarray(q, np.float64)
     v = np.ascontiguousarray(v, np.float64)
@@ -437,6 +444,7 @@ class Model:
     def __init__(self, spec, material: dict, precision: str | int = "mixed", dt: float = 0.0, bc=None, **kw):
         prec = precision if isinstance(precision, int) else (LDPM_MIXED if precision == "mixed" else LDPM_FP64)
         self.N, self.T, self.F = spec.n_particles, spec.n_tets, spec.n_facets
+        self._stream = kw.get("stream")
         self.h = ldpm_create(spec, material, prec, dt=dt, bc=bc, **kw)
         info, self.dt = ldpm_info(self.h)
 
@@ -456,6 +464,23 @@ class Model:
 
     def get_state(self, hist: bool = True):
         return ldpm_get_state(self.h, self.N, self.F, hist)
+
+    def get_state_device(self, hist: bool = True, device=None):
+        """The state as torch tensors on the device (torch only allocates the buffers; the library's
+        kernels fill them on its stream, which the caller's current stream then waits on)."""
+        import torch
+
+        dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        q = torch.empty((self.N, 6), dtype=torch.float64, device=dev)
+        v = torch.empty((self.N, 6), dtype=torch.float64, device=dev)
+        h5 = torch.empty((self.F, 5), dtype=torch.float64, device=dev) if hist else None
+        st = torch.empty((1,), dtype=torch.int64, device=dev)
+        ldpm_get_state_device(self.h, q.data_ptr(), v.data_ptr(), h5.data_ptr() if hist else 0, st.data_ptr())
+        if isinstance(self._stream, torch.cuda.Stream):
+            torch.cuda.current_stream(dev).wait_stream(self._stream)
+        else:  # a library-owned or raw stream: wait for it
+            ldpm_sync(self.h)
+        return q, v, h5, st
 
     def set_state(self, q, v, hist5=None, step: int = 0):
         ldpm_set_state(self.h, q, v, hist5, step)
