@@ -3,13 +3,17 @@
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
 
-One "step" is one explicit central-difference step of the whole specimen (half kick and drift, facet
-pass, particle pass).  The default workload is the uniaxial-tension cube (50 mm, d = 2..4 mm,
-~1.8M facets) in mixed precision (FP32 facets, FP64 particle state); the same workload is also
-measured in FP64.  L2 is flushed (a 512 MB write) before every timed step and the flush is outside
-the timed intervals.  With --gpus N > 1 (torchrun) every rank steps its own replica of the specimen
-(the explicit step has no exchange between independent specimens: weak scaling, replicas only).
-Prints one JSON line on rank 0.
+One "step" is one explicit central-difference step of the whole specimen (facet pass, particle pass
+with the half kicks, drift and energy sums).  The default workload is the largest single-GPU
+specimen, the confined-compression cube (100 mm, d = 3..6 mm, ~12.5M facets), in mixed precision
+(FP32 facet pass, FP64 particle state); the same workload is also measured in FP64, and the
+uniaxial-tension cube (50 mm, ~1.8M facets) is reported beside it.  Every arm uses the workload's
+fixed time step and times the steps that follow the workload's pre-roll of its loading history and
+W warm-up steps.  Where a step's working set is below four times the 129 MB L2, the L2 is flushed (a
+512 MB write) before every timed step, outside the timed intervals; above that the K steps run back to
+back.  With --gpus N > 1 (torchrun) every rank steps its own replica of the specimen (the explicit
+step has no exchange between independent specimens: weak scaling, replicas only).  Prints one JSON
+line on rank 0.
 """
 from __future__ import annotations
 
@@ -31,7 +35,21 @@ sys.path.insert(0, ROOT)
 METRIC = "facet-updates/s per explicit step and % of HBM roofline, mixed vs FP64"
 UNIT = "facet-updates/s"
 
-# Algorithmic bytes of one facet-pass launch: values the method reads or writes once per step.
+# Algorithmic bytes per facet-update of a layout that stores each facet's frame (I, J, n, m, c_I, A,
+# l: 52 B mixed / 96 B FP64), reads and writes the history (t_N, t_M, t_L, e_max: 32 / 64 B), writes
+# the facet force (12 / 24 B) and amortises the tetrahedron (ids, shape-function gradients: ~5 / 9 B)
+# over its 12 facets: 101 B (mixed) / 193 B (FP64) for the facet pass alone.  The whole step adds the
+# force re-read and the CSR gather with its moment arms and the particle state: 178 / 334 B.  The
+# headline roofline fractions use these per-unit figures; the library's own layout moves fewer bytes
+# (frames rebuilt from the staged positions, per-tetrahedron vertex shares instead of per-facet
+# forces), given beside them as the design-byte fractions.
+STORED_LAYOUT_BYTES_PER_FACET = {"mixed": {"facet_pass": 101.0, "step": 178.0},
+                                 "fp64": {"facet_pass": 193.0, "step": 334.0}}
+L2_BYTES = 129e6
+
+
+# Algorithmic bytes of one facet-pass launch in the library's own layout: values it reads or writes
+# once per step.
 #   per facet        geometry (arm c_I, area A) 4r, history read + written 8r
 #   per tetrahedron  4 particle ids 16 B, its 4 vertex force/moment shares written 24r
 #   per particle     the record the pass gathers once: mixed 21 floats (x, u as hi/lo pairs,
@@ -40,7 +58,7 @@ def facet_pass_bytes(F: int, T: int, N: int, r: int) -> float:
     return F * 12 * r + T * (16 + 24 * r) + N * (84 if r == 4 else 120)
 
 
-# Algorithmic bytes of one particle-pass launch.
+# Algorithmic bytes of one particle-pass launch in the library's own layout.
 #   per tetrahedron  4 CSR slot ids (4 B) and the 4 shares read (24r)
 #   per particle     row pointer 4 B; q, v read and written 192 B; forces and energy sums read and
 #                    written 128 B; inverse masses, BC codes, specimen 64 B; mixed mode writes the
@@ -195,15 +213,41 @@ def make_inputs(workload: str):
     return wl, spec, bc
 
 
-def time_steps(model, ldpm, torch, stream, flush, steps: int, warmup: int, profile: bool):
-    """Per-step device time (CUDA events on the library's stream), L2 flushed before every step."""
+def needs_flush(F: int, T: int, N: int, r: int) -> bool:
+    """A step whose working set is below four times the L2 could be partly served from L2 across steps:
+    flush between timed steps.  Larger ones run back to back."""
+    return facet_pass_bytes(F, T, N, r) + gather_pass_bytes(T, N, r) < 4 * L2_BYTES
+
+
+def run_preroll(model, preroll: int, steps: int):
+    """The pre-roll, ending with one call of `steps` steps, so that the CUDA graphs of a later
+    ldpm_step(steps) are captured before any timed region."""
+    if preroll >= steps > 0:
+        model.step(preroll - steps)
+        model.step(steps)
+    else:
+        model.step(preroll)
+
+
+def time_window(model, torch, stream, flush, steps: int, warmup: int):
+    """Device time of `steps` steps (CUDA events on the library's stream), after `warmup` untimed ones.
+    With a flush buffer: one step per ldpm_step call, the L2 flushed before each, the per-step
+    intervals summed.  Without: one ldpm_step call for all the steps, timed as one interval."""
     for _ in range(warmup):
-        with torch.cuda.stream(stream):
-            flush.zero_()
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
         model.step(1)
     stream.synchronize()
-    if profile:
-        ldpm.ldpm_profile(model.h, True)
+    if flush is None:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+        model.step(steps)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        stream.synchronize()
+        return a.elapsed_time(b)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     for a, b in ev:
         with torch.cuda.stream(stream):
@@ -213,76 +257,118 @@ def time_steps(model, ldpm, torch, stream, flush, steps: int, warmup: int, profi
         with torch.cuda.stream(stream):
             b.record(stream)
     stream.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ev]
-    kern = None
-    if profile:
-        kms, kcnt = ldpm.ldpm_profile_read(model.h)
-        ldpm.ldpm_profile(model.h, False)
-        kern = {"kick": (kms[0], int(kcnt[0])), "facet": (kms[1], int(kcnt[1])), "gather": (kms[2], int(kcnt[2]))}
-    return ms, kern
+    return sum(a.elapsed_time(b) for a, b in ev)
+
+
+def kernel_split(model, ldpm, torch, stream, flush, steps: int):
+    """Per-kernel device times of `steps` more steps: the library's profiling mode launches each
+    step's two kernels directly with an event before, between and after them (so the two times add up
+    to the step), with the same L2 treatment as the timed window."""
+    ldpm.ldpm_profile(model.h, True)
+    if flush is None:
+        model.step(steps)
+    else:
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            model.step(1)
+    stream.synchronize()
+    kms, kcnt = ldpm.ldpm_profile_read(model.h)
+    ldpm.ldpm_profile(model.h, False)
+    return kms[1] / max(1, kcnt[1]), kms[2] / max(1, kcnt[2])
+
+
+def hbm_roofline(units_bytes: float, design_bytes: float, ms: float, peak: float, peak_src: str, traffic,
+                 what: str):
+    """HBM roofline of one launch (or step): achieved = algorithmic bytes / device time."""
+    achieved = units_bytes / (ms * 1e-3) / 1e9
+    design = design_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": traffic, "algorithmic_bytes_per_launch": units_bytes, "bytes_model": what,
+            "frac_design_bytes": design / peak, "design_bytes_per_launch": design_bytes,
+            "peak_source": peak_src}
+
+
+def run_leg(name, wl, spec, bc, prec, steps, warmup, preroll, stream, flush_buf, peak, peak_src, world,
+            launch_mode=None):
+    """One workload in one precision: create (fixed dt), pre-roll, warm-up, K timed steps, the
+    per-kernel split, the rooflines and the energy check."""
+    import torch
+
+    from paper_2603_13190_gb300 import ldpm
+
+    N, T, F = spec.n_particles, spec.n_tets, spec.n_facets
+    r = 4 if prec == "mixed" else 8
+    flush = flush_buf if needs_flush(F, T, N, r) else None
+    model = ldpm.Model(spec, wl.material, precision=prec, dt=wl.dt, bc=bc, stream=stream)
+    if launch_mode is not None:
+        ldpm.ldpm_set_launch_mode(model.h, launch_mode)
+    run_preroll(model, preroll, steps)
+    barrier(world)
+    torch.cuda.synchronize()
+    tot = barrier_max(world, time_window(model, torch, stream, flush, steps, warmup))
+    facet_ms, gather_ms = kernel_split(model, ldpm, torch, stream, flush, steps)
+    energy, _ = model.energy()
+    mode = ldpm.ldpm_launch_mode(model.h) if hasattr(ldpm, "ldpm_launch_mode") else None
+    model.close()
+    ms_step = tot / steps
+    fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(T, N, r)
+    ref = STORED_LAYOUT_BYTES_PER_FACET[prec]
+    kern = "facet_warp_kernel" if prec == "mixed" else "facet_kernel"
+    return {
+        "workload": name, "precision": prec, "steps": steps, "value": job_value(world, F, steps, tot),
+        "ms_per_step": ms_step, "dt_s": wl.dt, "launch_mode": mode,
+        "l2": ("flushed (512 MB write) before every timed step, outside the timed interval" if flush is not None
+               else "working set %.0f MB > 4 x L2 (129 MB): steps back to back, no flush" % ((fb + gb) / 1e6)),
+        "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
+            preroll + warmup, preroll + warmup + steps, preroll, warmup),
+        "kernel_ms": {"facet": facet_ms, "gather": gather_ms,
+                      "sum_over_step": (facet_ms + gather_ms) / ms_step,
+                      "how": "profiling pass of K more steps: events before, between and after each step's "
+                             "two kernels (direct launches)"},
+        "roofline": hbm_roofline(ref["facet_pass"] * F, fb, facet_ms, peak, peak_src,
+                                 recorded_traffic(kern, name, prec),
+                                 "%.0f B per facet-update (facet pass of a stored-frame layout)" % ref["facet_pass"]),
+        "gather_roofline": hbm_roofline(gb, gb, gather_ms, peak, peak_src, None, "design bytes (no stored-layout "
+                                                                                 "figure for the pass alone)"),
+        "step_roofline": hbm_roofline(ref["step"] * F, fb + gb, ms_step, peak, peak_src, None,
+                                      "%.0f B per facet-update (whole step of a stored-frame layout)" % ref["step"]),
+        "energy_err_pct": float(energy[3]),
+        "sizes": {"particles": N, "tets": T, "facets": F},
+    }
 
 
 def run_ours(args, rank, world, local):
     import torch
 
-    from paper_2603_13190_gb300 import ldpm
+    from paper_2603_13190_gb300 import ldpm, workloads
 
     torch.cuda.set_device(local)
     wl, spec, bc = make_inputs(args.workload)
     N, T, F = spec.n_particles, spec.n_tets, spec.n_facets
+    preroll = wl.preroll if args.preroll is None else args.preroll
+    # the oracle's pre-roll and timed window run on a host core meanwhile (a separate process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = OracleWindow(spec, wl, bc, preroll + args.warmup)
     stream = torch.cuda.Stream()
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     peak, peak_src = measured_peaks()
-    out = {}
-    dt0 = None
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.__enter__()
-    for prec, steps in (("mixed", args.steps), ("fp64", max(3, args.steps // 4))):
-        model = ldpm.Model(spec, wl.material, precision=prec, dt=dt0 or 0.0, bc=bc, stream=stream, device=local)
-        dt0 = dt0 or model.dt
-        model.step(args.preroll)
-        barrier(world)
-        torch.cuda.synchronize()
-        ms, _ = time_steps(model, ldpm, torch, stream, flush, steps, args.warmup, profile=False)
-        torch.cuda.synchronize()
-        barrier(world)
-        tot = barrier_max(world, sum(ms))
-        # per-kernel durations from events around each launch (same stream), separate pass
-        _, kern = time_steps(model, ldpm, torch, stream, flush, steps, 1, profile=True)
-        r = 4 if prec == "mixed" else 8
-        fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(T, N, r)
-        facet_ms = kern["facet"][0] / max(1, kern["facet"][1])
-        gather_ms = kern["gather"][0] / max(1, kern["gather"][1])
-        achieved = fb / (facet_ms * 1e-3) / 1e9
-        # steady state: back-to-back steps from one captured graph, no flush (L2 may hold data)
-        model.step(args.warmup)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        nss = max(10, steps)
-        with torch.cuda.stream(stream):
-            e0.record(stream)
-        model.step(nss)
-        with torch.cuda.stream(stream):
-            e1.record(stream)
-        stream.synchronize()
-        ss_ms = e0.elapsed_time(e1) / nss
-        energy, _ = model.energy()
-        out[prec] = dict(
-            steps=steps, ms=ms, total_ms=tot, value=job_value(world, F, steps, tot),
-            facet_ms=facet_ms, gather_ms=gather_ms, kick_ms=kern["kick"][0] / max(1, kern["kick"][1]),
-            roofline={"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                      "traffic": recorded_traffic("facet_warp_kernel" if prec == "mixed" else "facet_kernel",
-                                                  args.workload, prec),
-                      "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
-            gather_roofline={"achieved": gb / (gather_ms * 1e-3) / 1e9, "frac": gb / (gather_ms * 1e-3) / 1e9 / peak,
-                             "algorithmic_bytes_per_launch": gb},
-            step_roofline={"achieved": (fb + gb) / (tot / steps * 1e-3) / 1e9,
-                           "frac": (fb + gb) / (tot / steps * 1e-3) / 1e9 / peak,
-                           "algorithmic_bytes_per_step": fb + gb},
-            steady_state={"facet_updates_per_s": world * F / (ss_ms * 1e-3), "ms_per_step": ss_ms,
-                          "l2": "not flushed (graph replay, back-to-back)"},
-            energy_err_pct=float(energy[3]), dt=model.dt)
-        model.close()
+    mixed = run_leg(args.workload, wl, spec, bc, "mixed", args.steps, args.warmup, preroll, stream, flush, peak,
+                    peak_src, world)
+    fp64 = run_leg(args.workload, wl, spec, bc, "fp64", max(3, args.steps // 4), args.warmup, preroll, stream, flush,
+                   peak, peak_src, world)
+    fp64["alu_roofline"] = fp64_alu_roofline(args.workload, fp64["kernel_ms"]["facet"])
+    extra = {}
+    if not args.no_extra and args.workload != "uniaxial_tension":
+        # the 1.82M-facet uniaxial-tension cube beside the headline
+        w2, s2, b2 = make_inputs("uniaxial_tension")
+        extra["uniaxial_tension"] = run_leg("uniaxial_tension", w2, s2, b2, "mixed", args.steps, args.warmup,
+                                            w2.preroll, stream, flush, peak, peak_src, world)
+        del s2
     if sampler:
         sampler.__exit__()
     clocks = sampler.summary() if sampler else None
@@ -292,7 +378,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.synchronize()
     K = args.steps
     t0 = time.perf_counter()
-    m = ldpm.Model(spec, wl.material, precision="mixed", dt=dt0, bc=bc, device=local)
+    m = ldpm.Model(spec, wl.material, precision="mixed", dt=wl.dt, bc=bc, device=local)
     for _ in range(K):
         m.step(1)
         m.energy()
@@ -303,30 +389,23 @@ def run_ours(args, rank, world, local):
     geo_bytes = spec.x.nbytes + spec.diameter.nbytes + spec.tets.nbytes + 3 * 4 * F + spec.facet_vtx.nbytes + \
         bc.mask.nbytes + bc.vel.nbytes + bc.v0.nbytes
     d2h = K * (16 * 8) + q.nbytes + v.nbytes + h5.nbytes
-    mx = out["mixed"]
     res = {
-        "metric": METRIC, "value": mx["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": mx["total_ms"] / mx["steps"], "higher_is_better": True,
+        "metric": METRIC, "value": mixed["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": mixed["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
                    "particles": N, "tets": T, "facets": F, "precision": "mixed: FP32 facet pass, FP64 particle state",
-                   "dt_s": dt0, "l2": "flushed (512 MB write) before every timed step, outside the timed interval",
-                   "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
-                       args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll, args.warmup),
+                   "dt_s": wl.dt, "l2": mixed["l2"], "timed_window": mixed["timed_window"],
+                   "launch_mode": mixed["launch_mode"],
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": wl.seed},
-        "roofline": mx["roofline"],
-        "gather_roofline": mx["gather_roofline"],
-        "step_roofline": mx["step_roofline"],
-        "kernel_ms": {"kick": mx["kick_ms"], "facet": mx["facet_ms"], "gather": mx["gather_ms"]},
-        "steady_state": mx["steady_state"],
-        "fp64": {"value": out["fp64"]["value"], "ms_per_step": out["fp64"]["total_ms"] / out["fp64"]["steps"],
-                 "steps": out["fp64"]["steps"], "roofline": out["fp64"]["roofline"],
-                 "step_roofline": out["fp64"]["step_roofline"],
-                 "kernel_ms": {"kick": out["fp64"]["kick_ms"], "facet": out["fp64"]["facet_ms"],
-                               "gather": out["fp64"]["gather_ms"]},
-                 "steady_state": out["fp64"]["steady_state"],
-                 "alu_roofline": fp64_alu_roofline(args.workload, out["fp64"]["facet_ms"])},
-        "mixed_over_fp64": mx["value"] / out["fp64"]["value"],
+        "roofline": mixed["roofline"],
+        "gather_roofline": mixed["gather_roofline"],
+        "step_roofline": mixed["step_roofline"],
+        "kernel_ms": mixed["kernel_ms"],
+        "energy_err_pct": mixed["energy_err_pct"],
+        "fp64": {k: fp64[k] for k in ("value", "ms_per_step", "steps", "roofline", "step_roofline", "kernel_ms",
+                                      "alu_roofline", "energy_err_pct")},
+        "mixed_over_fp64": mixed["value"] / fp64["value"],
         "e2e": {"value": world * F * K / e2e_s, "unit": UNIT, "h2d_bytes_per_step": geo_bytes / K,
                 "d2h_bytes_per_step": d2h / K, "seconds": e2e_s,
                 "what": "ldpm_create from host arrays, K x (ldpm_step(1) + ldpm_energy read-back), "
@@ -334,7 +413,8 @@ def run_ours(args, rank, world, local):
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }
-    return res, spec, wl, bc, dt0
+    res.update(extra)
+    return res, spec, wl, bc, cpu
 
 
 def run_batch(args, rank, world, local):
@@ -363,28 +443,28 @@ def run_batch(args, rank, world, local):
     sampler = ClockSampler(local) if rank == 0 else None
     if sampler:
         sampler.__enter__()
+    preroll = 200 if args.preroll is None else args.preroll
+    fl = flush if needs_flush(F, T, N, 4) else None
     barrier(world)
     torch.cuda.synchronize()
-    b.step(args.preroll)
-    ms, _ = time_steps(b, ldpm, torch, stream, flush, args.steps, args.warmup, profile=False)
-    torch.cuda.synchronize()
-    barrier(world)
-    tot = barrier_max(world, sum(ms))
-    _, kern = time_steps(b, ldpm, torch, stream, flush, args.steps, 1, profile=True)
+    run_preroll(b, preroll, args.steps)
+    tot = barrier_max(world, time_window(b, torch, stream, fl, args.steps, args.warmup))
+    facet_ms, gather_ms = kernel_split(b, ldpm, torch, stream, fl, args.steps)
     if sampler:
         sampler.__exit__()
-    facet_ms = kern["facet"][0] / max(1, kern["facet"][1])
-    gather_ms = kern["gather"][0] / max(1, kern["gather"][1])
     fb, gb = facet_pass_bytes(F, T, N, 4), gather_pass_bytes(T, N, 4)
-    achieved = fb / (facet_ms * 1e-3) / 1e9
+    ref = STORED_LAYOUT_BYTES_PER_FACET["mixed"]
     shape = b.launch_shape()
     errs = [float(b.energy(i)[0][3]) for i in range(len(b))]
     b.close()
     # all-FP64 single-specimen path, same GPU: the batch's first specimen
     single = ldpm.Model(specs[0], mats[0], precision="fp64", bc=bcs[0], stream=stream, device=local)
-    single.step(args.preroll)
-    ms64, _ = time_steps(single, ldpm, torch, stream, flush, max(3, args.steps // 4), args.warmup, profile=False)
-    fp64_single = specs[0].n_facets * len(ms64) / (sum(ms64) * 1e-3)
+    s0 = specs[0]
+    n64 = max(3, args.steps // 4)
+    run_preroll(single, preroll, n64)
+    ms64 = time_window(single, torch, stream, flush if needs_flush(s0.n_facets, s0.n_tets, s0.n_particles, 8) else None,
+                       n64, args.warmup)
+    fp64_single = specs[0].n_facets * n64 / (ms64 * 1e-3)
     single.close()
     value = job_value(world, F, args.steps, tot)
     return {
@@ -397,13 +477,17 @@ def run_batch(args, rank, world, local):
                                                                                  max(sp.n_particles for sp in specs)],
                    "precision": "mixed: FP32 facet pass, FP64 particle state",
                    "launch_shape": {"tets_per_block": shape[0], "lanes_per_particle": shape[1], "by": "autotuner"},
-                   "l2": "flushed (512 MB write) before every timed step, outside the timed interval",
+                   "l2": ("flushed (512 MB write) before every timed step, outside the timed interval" if fl is not None
+                          else "working set %.1f GB > 4 x L2 (129 MB): steps back to back, no flush" % ((fb + gb) / 1e9)),
                    "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
-                       args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll, args.warmup),
+                       preroll + args.warmup, preroll + args.warmup + args.steps, preroll, args.warmup),
+                   "dt_s": "per specimen, 0.9 x its critical step (power iteration at create)",
                    "generation_s": round(gen_s, 1), "create_s": round(create_s, 1)},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "algorithmic_bytes_per_launch": fb, "peak_source": peak_src},
-        "kernel_ms": {"facet": facet_ms, "gather": gather_ms},
+        "roofline": hbm_roofline(ref["facet_pass"] * F, fb, facet_ms, peak, peak_src, None,
+                                 "%.0f B per facet-update (facet pass of a stored-frame layout)" % ref["facet_pass"]),
+        "step_roofline": hbm_roofline(ref["step"] * F, fb + gb, tot / args.steps, peak, peak_src, None,
+                                      "%.0f B per facet-update (whole step of a stored-frame layout)" % ref["step"]),
+        "kernel_ms": {"facet": facet_ms, "gather": gather_ms, "sum_over_step": (facet_ms + gather_ms) / (tot / args.steps)},
         "fp64_single_specimen": {"value": fp64_single, "facets": specs[0].n_facets},
         "batched_mixed_over_fp64_single": value / fp64_single,
         "max_energy_error_pct": max(errs),
@@ -451,7 +535,7 @@ def run_adjoint(args, rank, world, local):
     stream = torch.cuda.Stream()
     peak, peak_src = measured_peaks()
     sampler = ClockSampler(local) if rank == 0 else None
-    m = ldpm.Model(spec, wl.material, precision="mixed", bc=bc, stream=stream, device=local)
+    m = ldpm.Model(spec, wl.material, precision="mixed", dt=wl.dt, bc=bc, stream=stream, device=local)
     dt = m.dt
     start = ldpm.ldpm_save_checkpoint(m.h)
     for _ in range(args.warmup):
@@ -580,23 +664,10 @@ def cpu_baseline_adjoint(spec, wl, bc, dt, budget_s: float = 20.0):
                       "%.1f s, single thread); the oracle has no reverse mode" % (n, spec.n_facets, el)}
 
 
-def cpu_baseline(spec, wl, bc, dt, budget_s: float = 20.0):
-    """The FP64 oracle as it stands, single thread on the host, on a bounded sample of the workload."""
-    import oracle
-
-    o = oracle.Oracle(spec, wl.material, dt, bc)
-    o.step(1)
-    n, t0 = 0, time.perf_counter()
-    while time.perf_counter() - t0 < budget_s and n < 200:
-        o.step(1)
-        n += 1
-    el = time.perf_counter() - t0
-    return {"value": spec.n_facets * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d explicit steps of the full %d-facet specimen (%.1f s, single thread)" % (n, spec.n_facets, el)}
-
-
-# One oracle process of the all-cores baseline: rebuilds the problem from a saved file, steps once,
-# reports ready, waits for the start line on stdin, then steps until its time budget is spent.
+# One oracle process of the CPU baseline.  argv: repo root, problem file, JSON arguments.  It rebuilds
+# the problem, runs the pre-roll (and warm-up) of the loading history, writes the state it reached to
+# the state file, and then (single mode) times whole steps until its time budget is spent, or (cores
+# mode) reports ready, loads that state, waits for the start line on stdin and times its window.
 _ORACLE_WORKER = r"""
 import json, sys, time
 import numpy as np
@@ -610,52 +681,92 @@ spec = Specimen(x=z['x'], diameter=z['diameter'], tets=z['tets'], facet_pi=z['fa
                 facet_tet=z['facet_tet'], facet_vtx=z['facet_vtx'], edge=a['edge'], d_min=a['d_min'], d_max=a['d_max'])
 bc = BoundaryConditions(mask=z['mask'], vel=z['vel'], ramp_time=a['ramp_time'], v0=z['v0'])
 o = oracle.Oracle(spec, a['material'], a['dt'], bc)
-o.step(1)
-print('ready', flush=True)
-sys.stdin.readline()
-n, t0 = 0, time.perf_counter()
-while time.perf_counter() - t0 < a['budget_s']:
-    o.step(1)
-    n += 1
-print(json.dumps({'steps': n, 'seconds': time.perf_counter() - t0}), flush=True)
+if a['mode'] == 'single':
+    t0 = time.perf_counter()
+    o.step(a['preroll'])
+    pre_s = time.perf_counter() - t0
+    q, v, h5, st = o.get_state()
+    np.savez(a['state'], q=q, v=v, h5=h5, step=st)
+    n, t0 = 0, time.perf_counter()
+    while n < 1 or time.perf_counter() - t0 < a['budget_s']:
+        o.step(1)
+        n += 1
+    print(json.dumps({'steps': n, 'seconds': time.perf_counter() - t0, 'preroll_s': pre_s}), flush=True)
+else:
+    s = np.load(a['state'])
+    o.set_state(s['q'], s['v'], s['h5'], int(s['step']))
+    print('ready', flush=True)
+    sys.stdin.readline()
+    n, t0 = 0, time.perf_counter()
+    while n < 1 or time.perf_counter() - t0 < a['budget_s']:
+        o.step(1)
+        n += 1
+    print(json.dumps({'steps': n, 'seconds': time.perf_counter() - t0}), flush=True)
 """
 
 
-def cpu_all_cores(spec, wl, bc, dt, budget_s: float = 10.0, max_procs: int = 16):
-    """The oracle on all host cores: one single-thread oracle process per core, each stepping its own
-    copy of the full specimen over the same time window; the value is the sum of their rates (the
-    host's aggregate throughput on independent copies of the workload; the oracle itself is not
-    parallelised).  Processes are started with subprocess, so none is forked from this one.  Returns
-    None with the reason on any failure."""
-    import tempfile
+class OracleWindow:
+    """The FP64 oracle as it stands, single thread, on the same workload, time step and window as the
+    GPU arm: a separate process (started with subprocess, never forked from a process holding a CUDA
+    context) runs the pre-roll and warm-up of the loading history while the GPU is measured, then times
+    whole steps for about `budget_s`.  The state it reached is kept for the all-cores figure."""
 
-    cores = os.cpu_count() or 1
-    avail_gb = 8.0
-    try:  # memory the kernel can hand out without swapping (free pages plus reclaimable cache)
-        with open("/proc/meminfo") as mi:
-            avail_gb = next(int(l.split()[1]) for l in mi if l.startswith("MemAvailable:")) / 2 ** 20
-    except (OSError, StopIteration, ValueError):
+    def __init__(self, spec, wl, bc, preroll: int, budget_s: float = 20.0):
+        import tempfile
+
+        self.spec, self.wl, self.bc, self.preroll = spec, wl, bc, preroll
+        self.dir = tempfile.TemporaryDirectory(prefix="oracle_window_")
+        self.problem = os.path.join(self.dir.name, "problem.npz")
+        self.state = os.path.join(self.dir.name, "state.npz")
+        np.savez(self.problem, x=spec.x, diameter=spec.diameter, tets=spec.tets, facet_pi=spec.facet_pi,
+                 facet_pj=spec.facet_pj, facet_tet=spec.facet_tet, facet_vtx=spec.facet_vtx, mask=bc.mask, vel=bc.vel,
+                 v0=bc.v0)
+        self.base = {"edge": spec.edge, "d_min": spec.d_min, "d_max": spec.d_max, "ramp_time": bc.ramp_time,
+                     "material": dict(wl.material), "dt": wl.dt, "state": self.state}
+        a = json.dumps(dict(self.base, mode="single", preroll=preroll, budget_s=budget_s))
+        self.proc = subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, ROOT, self.problem, a], cwd=ROOT,
+                                     stdin=subprocess.DEVNULL, stdout=subprocess.PIPE, stderr=subprocess.PIPE,
+                                     text=True)
+
+    def result(self, timeout_s: float = 1800.0):
         try:
-            avail_gb = os.sysconf("SC_AVPHYS_PAGES") * os.sysconf("SC_PAGE_SIZE") / 2 ** 30
-        except (ValueError, OSError):
+            out, err = self.proc.communicate(timeout=timeout_s)
+            r = json.loads(out.strip().splitlines()[-1])
+        except Exception as e:
+            if self.proc.poll() is None:
+                self.proc.kill()
+            return {"value": None, "reason": "%s: %s" % (type(e).__name__, e)}
+        return {"value": self.spec.n_facets * r["steps"] / r["seconds"], "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d explicit steps of the full %d-facet specimen after its %d-step pre-roll and warm-up "
+                          "(%.1f s timed, single thread; dt %.4g s, the GPU arm's)"
+                          % (r["steps"], self.spec.n_facets, self.preroll, r["seconds"], self.wl.dt)}
+
+    def all_cores(self, budget_s: float = 10.0, max_procs: int = 16):
+        """The oracle on all host cores: one single-thread oracle process per core, each starting from
+        the pre-rolled state and stepping its own copy of the full specimen over the same time window;
+        the value is the sum of their rates (the host's aggregate throughput on independent copies of the
+        workload; the oracle itself is not parallelised).  Returns the reason on any failure."""
+        cores = os.cpu_count() or 1
+        avail_gb = 8.0
+        try:  # memory the kernel can hand out without swapping (free pages plus reclaimable cache)
+            with open("/proc/meminfo") as mi:
+                avail_gb = next(int(l.split()[1]) for l in mi if l.startswith("MemAvailable:")) / 2 ** 20
+        except (OSError, StopIteration, ValueError):
             pass
-    per_gb = 1.0 + spec.n_facets * 400 / 2 ** 30  # interpreter and libraries, plus the oracle's arrays
-    C = int(max(1, min(cores, max_procs, avail_gb // (2 * per_gb))))
-    procs = []
-    with tempfile.TemporaryDirectory(prefix="oracle_cores_") as d:
-        f = os.path.join(d, "problem.npz")
-        np.savez(f, x=spec.x, diameter=spec.diameter, tets=spec.tets, facet_pi=spec.facet_pi, facet_pj=spec.facet_pj,
-                 facet_tet=spec.facet_tet, facet_vtx=spec.facet_vtx, mask=bc.mask, vel=bc.vel, v0=bc.v0)
-        a = json.dumps({"edge": spec.edge, "d_min": spec.d_min, "d_max": spec.d_max, "ramp_time": bc.ramp_time,
-                        "material": dict(wl.material), "dt": dt, "budget_s": budget_s})
+        per_gb = 1.0 + self.spec.n_facets * 500 / 2 ** 30  # interpreter, libraries, the oracle's arrays
+        C = int(max(1, min(cores, max_procs, avail_gb // (2 * per_gb))))
+        if not os.path.exists(self.state):
+            return {"value": None, "reason": "the single-thread oracle process did not reach the window"}
+        a = json.dumps(dict(self.base, mode="cores", budget_s=budget_s))
+        procs = []
         try:
             for _ in range(C):
-                procs.append(subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, ROOT, f, a], cwd=ROOT,
+                procs.append(subprocess.Popen([sys.executable, "-c", _ORACLE_WORKER, ROOT, self.problem, a], cwd=ROOT,
                                               stdin=subprocess.PIPE, stdout=subprocess.PIPE,
                                               stderr=subprocess.DEVNULL, text=True))
             import select
 
-            deadline = time.monotonic() + 300.0
+            deadline = time.monotonic() + 600.0
             for pr in procs:
                 left = deadline - time.monotonic()
                 if left <= 0 or not select.select([pr.stdout], [], [], left)[0] or \
@@ -666,19 +777,24 @@ def cpu_all_cores(spec, wl, bc, dt, budget_s: float = 10.0, max_procs: int = 16)
                 pr.stdin.flush()
             res = []
             for pr in procs:
-                out, _ = pr.communicate(timeout=budget_s + 120)
+                out, _ = pr.communicate(timeout=budget_s + 300)
                 res.append(json.loads(out.strip().splitlines()[-1]))
         except Exception as e:  # the GPU figures stand on their own: report why this one is missing
             for pr in procs:
                 if pr.poll() is None:
                     pr.kill()
             return {"value": None, "reason": "%s: %s" % (type(e).__name__, e)}
-    rate = sum(spec.n_facets * r["steps"] / r["seconds"] for r in res)
-    steps = [r["steps"] for r in res]
-    return {"value": rate, "unit": UNIT, "cores": C, "kind": "oracle",
-            "sample": "%d concurrent single-thread oracle processes (%d host cores), each stepping its own copy of "
-                      "the full %d-facet specimen for %.0f s (%d-%d steps each); sum of their rates"
-                      % (C, cores, spec.n_facets, budget_s, min(steps), max(steps))}
+        rate = sum(self.spec.n_facets * r["steps"] / r["seconds"] for r in res)
+        steps = [r["steps"] for r in res]
+        return {"value": rate, "unit": UNIT, "cores": C, "kind": "oracle",
+                "sample": "%d concurrent single-thread oracle processes (%d host cores), each stepping its own copy "
+                          "of the full %d-facet specimen from the pre-rolled state for %.0f s (%d-%d steps each); "
+                          "sum of their rates" % (C, cores, self.spec.n_facets, budget_s, min(steps), max(steps))}
+
+    def close(self):
+        if self.proc.poll() is None:
+            self.proc.kill()
+        self.dir.cleanup()
 
 
 def run_reference(args, rank, world):
@@ -690,9 +806,8 @@ def run_reference(args, rank, world):
     from paper_2603_13190_gb300 import workloads
 
     wl, spec, bc = make_inputs(args.workload)
-    o = oracle.Oracle(spec, wl.material, 1e-7, bc)
-    x0 = np.random.default_rng(0).standard_normal(6 * spec.n_particles)
-    dt = wl.dt_factor * 2.0 / np.sqrt(o.lambda_max(x0, 200))
+    dt = wl.dt  # the workload's fixed step, the one the GPU arm uses
+    preroll = wl.preroll if args.preroll is None else args.preroll
     o = oracle.Oracle(spec, wl.material, dt, bc)
     adjoint = args.workload.startswith("adjoint")
     if adjoint:
@@ -701,7 +816,7 @@ def run_reference(args, rank, world):
         seed = np.zeros((spec.n_particles, 6))
         seed[spec.face_nodes(2, 1), 2] = 1.0
         d = np.random.default_rng(0).standard_normal((8, spec.n_facets))
-    o.step(args.preroll)
+    o.step(preroll)
     for _ in range(args.warmup):
         o.step(1)
     t = []
@@ -718,7 +833,7 @@ def run_reference(args, rank, world):
     val = spec.n_facets * args.steps / tot
     what = ("%%d steps each carrying 8 directional derivatives (forward mode), after %d pre-roll and %%d warm-up "
             "steps, single thread" if adjoint else
-            "%%d full explicit steps after %d pre-roll and %%d warm-up steps, single thread") % args.preroll
+            "%%d full explicit steps after %d pre-roll and %%d warm-up steps, single thread") % preroll
     return {"impl": "reference", "metric": ADJ_METRIC if adjoint else METRIC, "value": val, "unit": UNIT,
             "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -727,7 +842,7 @@ def run_reference(args, rank, world):
                        "particles": spec.n_particles, "tets": spec.n_tets, "facets": spec.n_facets,
                        "precision": "FP64 oracle", "dt_s": dt, "seed": wl.seed,
                        "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
-                           args.preroll + args.warmup, args.preroll + args.warmup + args.steps, args.preroll,
+                           preroll + args.warmup, preroll + args.warmup + args.steps, preroll,
                            args.warmup)},
             "cpu_baseline": {"value": val, "unit": UNIT, "kind": "oracle", "cores": 1,
                              "sample": what % (args.steps, args.warmup)},
@@ -778,20 +893,21 @@ def main():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--workload", default="uniaxial_tension",
+    ap.add_argument("--workload", default="confined_compression",
                     choices=("uniaxial_tension", "confined_compression", "elastic_vibration",
                              "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--preroll", type=int, default=200,
-                    help="untimed steps of the loading history before the warm-up: the timed window then sees "
-                         "every facet strained (the loading wave crosses a 50 mm cube in about 60 steps; "
-                         "before that, facets at zero strain take the law's cheap path)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the uniaxial-tension line beside the headline")
+    ap.add_argument("--preroll", type=int, default=None,
+                    help="untimed steps of the loading history before the warm-up (default: the workload's own, "
+                         "enough for the loading wave to cross the specimen, so that the timed window sees every "
+                         "facet strained rather than the law's zero-strain path)")
     ap.add_argument("--counters", action="store_true",
                     help="print the algorithmic bytes of each kernel for the workload (per-unit figures and "
                          "totals per launch and per step) and exit; no GPU is used")
     ap.add_argument("--ncu-case", choices=("mixed", "fp64", "adjoint"), default=None,
-                    help="profiling target: create the workload (dt = 2e-7 s, no estimate), run the pre-roll, "
+                    help="profiling target: create the workload (its fixed dt), run the pre-roll, "
                          "then between profiler start and stop 4 steps with plain launches (adjoint: one "
                          "8-step ldpm_adjoint, checkpoints every 4 steps, on the adjoint workload in mixed "
                          "precision) and exit; nothing is timed")
@@ -807,8 +923,8 @@ def main():
         # the captured launches come after the pre-roll: run ncu with --profile-from-start off
         if args.ncu_case == "adjoint":
             wl, spec, bc = make_inputs("adjoint_uniaxial_tension")
-            m = ldpm.Model(spec, wl.material, precision="mixed", dt=2e-7, bc=bc, graph_chunk=-1)
-            m.step(args.preroll)
+            m = ldpm.Model(spec, wl.material, precision="mixed", dt=wl.dt, bc=bc, graph_chunk=-1)
+            m.step(200 if args.preroll is None else args.preroll)
             m.sync()
             seed = np.zeros((spec.n_particles, 6))
             seed[spec.face_nodes(2, 1), 2] = 1.0
@@ -816,8 +932,8 @@ def main():
             m.adjoint(8, seed, 4)
         else:
             wl, spec, bc = make_inputs(args.workload)
-            m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=2e-7, bc=bc, graph_chunk=-1)
-            m.step(args.preroll)
+            m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=wl.dt or 2e-7, bc=bc, graph_chunk=-1)
+            m.step(wl.preroll if args.preroll is None else args.preroll)
             m.sync()
             torch.cuda.profiler.start()
             m.step(4)
@@ -861,11 +977,14 @@ def main():
 
             dist.destroy_process_group()
         return
-    res, spec, wl, bc, dt = run_ours(args, rank, world, local)
+    res, spec, wl, bc, cpu = run_ours(args, rank, world, local)
     if rank == 0:
-        if world == 1 and not args.no_cpu_baseline:
-            res["cpu_baseline"] = cpu_baseline(spec, wl, bc, dt)
-            res["cpu_all_cores"] = cpu_all_cores(spec, wl, bc, dt)
+        if cpu is not None:
+            try:
+                res["cpu_baseline"] = cpu.result()
+                res["cpu_all_cores"] = cpu.all_cores()
+            finally:
+                cpu.close()
         print(json.dumps(res), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -199,9 +199,12 @@ int ldpm_set_bc(ldpm_t h, const int32_t *mask, const double *vel, double ramp_ti
 int ldpm_info(ldpm_t h, int64_t info[5], double *dt);
 
 /* Per-kernel CUDA-event timing of ldpm_step on the handle's stream.  enable = 1 starts (and
- * clears) recording, 0 stops.  ldpm_profile_read fills ms[k] (summed milliseconds) and count[k]
- * (launches) for k = 0 kick, 1 facet pass, 2 gather+update, 3 reverse facet pass and 4 reverse
- * particle pass (ldpm_adjoint); n = entries the caller provides (at most 5 are written). */
+ * clears) recording, 0 stops.  While recording, ldpm_step launches each step's two kernels directly
+ * (no graph) with an event before the facet pass, one between the passes and one after the particle
+ * pass, so the two kernel times of a step add up to its duration.  ldpm_profile_read fills ms[k]
+ * (summed milliseconds) and count[k] (launches) for k = 0 kick, 1 facet pass, 2 gather+update,
+ * 3 reverse facet pass and 4 reverse particle pass (ldpm_adjoint); n = entries the caller provides
+ * (at most 5 are written). */
 int ldpm_profile(ldpm_t h, int32_t enable);
 int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n);
 

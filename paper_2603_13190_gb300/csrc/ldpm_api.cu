@@ -5,6 +5,7 @@
 // particle-to-facet-end CSR list in a fixed order, upload, and the critical-step estimate.
 // Stepping (ldpm_step): the kernels of ldpm_kernels.cu, replayed from captured CUDA graphs.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -219,7 +220,7 @@ struct ldpm_ctx {
     std::map<int64_t, cudaGraphExec_t> graphs;
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
-    std::vector<std::pair<int, int>> ev_pairs;  // (kernel id, event index of start)
+    std::vector<std::array<int, 3>> ev_pairs;  // (kernel id, event index of start, event index of end)
     double prof_ms[5] = {0, 0, 0, 0, 0};  // kick, facet pass, particle pass, reverse facet, reverse particle
     int64_t prof_cnt[5] = {0, 0, 0, 0, 0};
     size_t rsize() const { return prec == LDPM_MIXED ? sizeof(float) : sizeof(double); }
@@ -1039,23 +1040,23 @@ int graph_for(ldpm_ctx *h, int64_t len, cudaGraphExec_t *exec)
 
 int enqueue_profiled(ldpm_ctx *h, int64_t nsteps)
 {
-    auto rec = [&](int kid, auto &&launch) -> int {
-        cudaEvent_t a, b;
-        if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
-            return fail(LDPM_E_CUDA, "event create failed");
-        h->ev_pool.push_back(a);
-        h->ev_pool.push_back(b);
-        h->ev_pairs.push_back({kid, (int)h->ev_pool.size() - 2});
-        CU(cudaEventRecord(a, h->stream));
-        int rc = launch();
-        if (rc) return rc;
-        CU(cudaEventRecord(b, h->stream));
-        return LDPM_OK;
-    };
+    // three events per step (before the facet pass, between the passes, after the particle pass): the
+    // two kernel times add up to the step's time, with no event between consecutive steps
     int rc;
     for (int64_t i = 0; i < nsteps; ++i) {
-        if ((rc = rec(1, [&]() { return launch_facet_any(h, FACET_STEP, nullptr); }))) return rc;
-        if ((rc = rec(2, [&]() { return launch_gather_any(h, GATHER_STEP_MID, nullptr); }))) return rc;
+        cudaEvent_t ev[3];
+        for (auto &e : ev) {
+            if (cudaEventCreate(&e) != cudaSuccess) return fail(LDPM_E_CUDA, "event create failed");
+            h->ev_pool.push_back(e);
+        }
+        const int i0 = (int)h->ev_pool.size() - 3;
+        h->ev_pairs.push_back({1, i0, i0 + 1});
+        h->ev_pairs.push_back({2, i0 + 1, i0 + 2});
+        CU(cudaEventRecord(ev[0], h->stream));
+        if ((rc = launch_facet_any(h, FACET_STEP, nullptr))) return rc;
+        CU(cudaEventRecord(ev[1], h->stream));
+        if ((rc = launch_gather_any(h, GATHER_STEP_MID, nullptr))) return rc;
+        CU(cudaEventRecord(ev[2], h->stream));
     }
     return LDPM_OK;
 }
@@ -1064,10 +1065,10 @@ int collect_profile(ldpm_ctx *h)
 {
     for (auto &pr : h->ev_pairs) {
         float ms = 0;
-        CU(cudaEventSynchronize(h->ev_pool[pr.second + 1]));
-        CU(cudaEventElapsedTime(&ms, h->ev_pool[pr.second], h->ev_pool[pr.second + 1]));
-        h->prof_ms[pr.first] += ms;
-        h->prof_cnt[pr.first] += 1;
+        CU(cudaEventSynchronize(h->ev_pool[pr[2]]));
+        CU(cudaEventElapsedTime(&ms, h->ev_pool[pr[1]], h->ev_pool[pr[2]]));
+        h->prof_ms[pr[0]] += ms;
+        h->prof_cnt[pr[0]] += 1;
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     h->ev_pool.clear();
@@ -1085,7 +1086,7 @@ int timed(ldpm_ctx *h, int kid, Fn &&launch)
         return fail(LDPM_E_CUDA, "event create failed");
     h->ev_pool.push_back(a);
     h->ev_pool.push_back(b);
-    h->ev_pairs.push_back({kid, (int)h->ev_pool.size() - 2});
+    h->ev_pairs.push_back({kid, (int)h->ev_pool.size() - 2, (int)h->ev_pool.size() - 1});
     CU(cudaEventRecord(a, h->stream));
     int rc = launch();
     if (rc) return rc;

@@ -86,6 +86,15 @@ class Workload:
     precision: str          # "fp64" or "mixed"
     steps: int
     dt_factor: float = 0.9
+    # Fixed time step of the benchmark runs (s): 0.9 of the critical step 2 / sqrt(lambda_max(M^-1 K))
+    # of the seeded specimen (the oracle's power iteration: 2.31e-7 s for the 50 mm cubes, 2.52e-7 s
+    # for the 100 mm cube, 4.60e-7 s for the 25 mm cube), rounded down, so that every arm of a
+    # comparison steps with the same dt.  0 = estimate per run.
+    dt: float = 0.0
+    # Untimed steps of the loading history before a benchmark's warm-up and timed window: enough for
+    # the loading wave (~1 mm per step) to cross the specimen, so that the timed steps see every facet
+    # strained rather than the law's zero-strain path.
+    preroll: int = 200
 
     def specimen(self) -> Specimen:
         return make_cube_specimen(self.edge, self.d_min, self.d_max, self.n_particles, self.seed)
@@ -197,13 +206,13 @@ def batch_specimens(n: int = 64, seed: int = 1, processes: int | None = None):
 
 WORKLOADS = {
     "elastic_vibration": Workload("elastic_vibration", 25.0, 4.0, 8.0, 420, 1, dict(WORKLOAD_MATERIAL, elastic=1),
-                                  "fp64", 2000),
+                                  "fp64", 2000, dt=4.1e-7, preroll=0),
     "uniaxial_tension": Workload("uniaxial_tension", 50.0, 2.0, 4.0, 25000, 1, dict(WORKLOAD_MATERIAL), "mixed",
-                                 200000),
+                                 200000, dt=2.0e-7, preroll=200),
     "confined_compression": Workload("confined_compression", 100.0, 3.0, 6.0, 165000, 1,
-                                     dict(WORKLOAD_MATERIAL), "mixed", 50000),
+                                     dict(WORKLOAD_MATERIAL), "mixed", 50000, dt=2.2e-7, preroll=100),
     "adjoint_uniaxial_tension": Workload("adjoint_uniaxial_tension", 50.0, 2.0, 4.0, 25000, 1,
-                                         dict(WORKLOAD_MATERIAL), "mixed", 5000),
+                                         dict(WORKLOAD_MATERIAL), "mixed", 5000, dt=2.0e-7, preroll=0),
 }
 # (the batched workload is built by batch_specimens / batch_recipe; material WORKLOAD_MATERIAL with
 # the friction of the workload definition: mu_0 = 0.2, mu_inf = 0, sigma_N0 = 600 MPa)

@@ -50,12 +50,34 @@ def test_fp64_alu_roofline_arithmetic(monkeypatch):
     assert abs(r["peak"] - 1.25856) < 1e-9 and abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-15
 
 
-def test_cpu_all_cores_sums_concurrent_oracle_processes():
-    """The all-cores oracle figure: independent oracle processes over one time window, rates summed."""
+def test_oracle_window_and_all_cores():
+    """The CPU baseline: one oracle process runs the pre-roll and warm-up of the loading history and
+    times the window after it; the all-cores figure starts independent oracle processes from the state
+    that process reached, over one time window, and sums their rates."""
     from paper_2603_13190_gb300 import workloads
 
     wl = workloads.WORKLOADS["elastic_vibration"]
     spec = wl.specimen()
-    r = bench.cpu_all_cores(spec, wl, workloads.workload_bc(wl.name, spec), 1e-7, budget_s=0.5, max_procs=2)
-    assert r["value"] > 0 and r["kind"] == "oracle" and 1 <= r["cores"] <= 2, r
-    assert "concurrent single-thread oracle processes" in r["sample"]
+    w = bench.OracleWindow(spec, wl, workloads.workload_bc(wl.name, spec), preroll=3, budget_s=0.3)
+    try:
+        r = w.result(timeout_s=300)
+        assert r["value"] > 0 and r["kind"] == "oracle" and r["cores"] == 1, r
+        assert "3-step pre-roll" in r["sample"] and ("dt %.4g s" % wl.dt) in r["sample"]
+        a = w.all_cores(budget_s=0.5, max_procs=2)
+        assert a["value"] > 0 and a["kind"] == "oracle" and 1 <= a["cores"] <= 2, a
+        assert "from the pre-rolled state" in a["sample"]
+    finally:
+        w.close()
+
+
+def test_reference_arm_uses_the_workload_time_step_and_window():
+    """Both arms step with the workload's fixed dt after the same pre-roll and warm-up."""
+    from paper_2603_13190_gb300 import workloads
+
+    wl = workloads.WORKLOADS["elastic_vibration"]
+    args = type("A", (), {"workload": "elastic_vibration", "warmup": 3, "steps": 2, "preroll": None})()
+    r = bench.run_reference(args, 0, 1)
+    assert r["impl"] == "reference" and r["config"]["dt_s"] == wl.dt and r["value"] > 0
+    assert "steps %d..%d" % (wl.preroll + 3, wl.preroll + 5) in r["config"]["timed_window"]
+    for name, w in workloads.WORKLOADS.items():
+        assert w.dt > 0, name
