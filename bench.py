@@ -204,6 +204,45 @@ def barrier(world: int):
         dist.barrier()
 
 
+LAUNCH_MODES = {"pairs": 1, "persistent": 2}
+
+
+def mode_compare(name, prec, steps, warmup, stream, flush_buf):
+    """K timed steps of one workload in each launch mode (same pre-roll and window), launch pairs
+    replayed from graphs against one persistent launch per ldpm_step call."""
+    import torch
+
+    from paper_2603_13190_gb300 import ldpm
+
+    wl, spec, bc = make_inputs(name)
+    r = 4 if prec == "mixed" else 8
+    flush = flush_buf if needs_flush(spec.n_facets, spec.n_tets, spec.n_particles, r) else None
+    out = {"precision": prec, "facets": spec.n_facets,
+           "l2": "flushed before the call of K steps" if flush is not None else "no flush (working set > 4 x L2)"}
+    for mode in ("pairs", "persistent"):
+        m = ldpm.Model(spec, wl.material, precision=prec, dt=wl.dt, bc=bc, stream=stream)
+        ldpm.ldpm_set_launch_mode(m.h, LAUNCH_MODES[mode])
+        run_preroll(m, wl.preroll, steps)
+        for _ in range(warmup):
+            m.step(1)
+        stream.synchronize()
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            a.record(stream)
+        m.step(steps)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        stream.synchronize()
+        ms = a.elapsed_time(b)
+        out[mode] = {"value": spec.n_facets * steps / (ms * 1e-3), "ms_per_step": ms / steps}
+        m.close()
+    out["persistent_over_pairs"] = out["persistent"]["value"] / out["pairs"]["value"]
+    return out
+
+
 def make_inputs(workload: str):
     from paper_2603_13190_gb300 import workloads
 
@@ -280,7 +319,8 @@ def kernel_split(model, ldpm, torch, stream, flush, steps: int):
 
 def hbm_roofline(units_bytes: float, design_bytes: float, ms: float, peak: float, peak_src: str, traffic,
                  what: str):
-    """HBM roofline of one launch (or step): achieved = algorithmic bytes / device time."""
+    """HBM roofline of one launch: achieved = algorithmic bytes (the per-unit figure `what` x units) /
+    device time, with the library layout's own bytes beside it."""
     achieved = units_bytes / (ms * 1e-3) / 1e9
     design = design_bytes / (ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -289,10 +329,23 @@ def hbm_roofline(units_bytes: float, design_bytes: float, ms: float, peak: float
             "peak_source": peak_src}
 
 
+def step_roofline(stored_bytes: float, design_bytes: float, ms: float, peak: float, peak_src: str):
+    """HBM roofline of a whole step on the bytes the library's layout moves (frac); the stored-frame
+    layout's per-step bytes over the same time (an effective rate, above the peak whenever that layout
+    would move more than this one does in the time) beside it."""
+    achieved = design_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "algorithmic_bytes_per_step": design_bytes, "bytes_model": "design bytes of both passes",
+            "frac_stored_layout_bytes": stored_bytes / (ms * 1e-3) / 1e9 / peak,
+            "stored_layout_bytes_per_step": stored_bytes, "peak_source": peak_src}
+
+
 def run_leg(name, wl, spec, bc, prec, steps, warmup, preroll, stream, flush_buf, peak, peak_src, world,
-            launch_mode=None):
-    """One workload in one precision: create (fixed dt), pre-roll, warm-up, K timed steps, the
-    per-kernel split, the rooflines and the energy check."""
+            launch="auto"):
+    """One workload in one precision: create (fixed dt; launch "auto": the library's autotuner picks the
+    launch shape and mode, else the named mode), pre-roll, warm-up, K timed steps, the per-kernel split
+    (from launch pairs on the same state: the persistent kernel has no per-pass split), the rooflines
+    and the energy check."""
     import torch
 
     from paper_2603_13190_gb300 import ldpm
@@ -300,16 +353,18 @@ def run_leg(name, wl, spec, bc, prec, steps, warmup, preroll, stream, flush_buf,
     N, T, F = spec.n_particles, spec.n_tets, spec.n_facets
     r = 4 if prec == "mixed" else 8
     flush = flush_buf if needs_flush(F, T, N, r) else None
-    model = ldpm.Model(spec, wl.material, precision=prec, dt=wl.dt, bc=bc, stream=stream)
-    if launch_mode is not None:
-        ldpm.ldpm_set_launch_mode(model.h, launch_mode)
+    model = ldpm.Model(spec, wl.material, precision=prec, dt=wl.dt, bc=bc, stream=stream, autotune=launch == "auto")
+    if launch != "auto":
+        ldpm.ldpm_set_launch_mode(model.h, LAUNCH_MODES[launch])
+    mode = ldpm.ldpm_launch_mode(model.h)
     run_preroll(model, preroll, steps)
     barrier(world)
     torch.cuda.synchronize()
     tot = barrier_max(world, time_window(model, torch, stream, flush, steps, warmup))
+    ldpm.ldpm_set_launch_mode(model.h, LAUNCH_MODES["pairs"])
     facet_ms, gather_ms = kernel_split(model, ldpm, torch, stream, flush, steps)
     energy, _ = model.energy()
-    mode = ldpm.ldpm_launch_mode(model.h) if hasattr(ldpm, "ldpm_launch_mode") else None
+    shape = model.launch_shape()
     model.close()
     ms_step = tot / steps
     fb, gb = facet_pass_bytes(F, T, N, r), gather_pass_bytes(T, N, r)
@@ -317,24 +372,33 @@ def run_leg(name, wl, spec, bc, prec, steps, warmup, preroll, stream, flush_buf,
     kern = "facet_warp_kernel" if prec == "mixed" else "facet_kernel"
     return {
         "workload": name, "precision": prec, "steps": steps, "value": job_value(world, F, steps, tot),
-        "ms_per_step": ms_step, "dt_s": wl.dt, "launch_mode": mode,
+        "ms_per_step": ms_step, "dt_s": wl.dt,
+        "launch": {"mode": {v: k for k, v in LAUNCH_MODES.items()}[mode], "by": "autotuner" if launch == "auto" else "set",
+                   "tets_per_block": int(shape[0]), "lanes_per_particle": int(shape[1])},
         "l2": ("flushed (512 MB write) before every timed step, outside the timed interval" if flush is not None
                else "working set %.0f MB > 4 x L2 (129 MB): steps back to back, no flush" % ((fb + gb) / 1e6)),
         "timed_window": "steps %d..%d of the loading history (%d untimed pre-roll steps, %d warm-up)" % (
             preroll + warmup, preroll + warmup + steps, preroll, warmup),
         "kernel_ms": {"facet": facet_ms, "gather": gather_ms,
-                      "sum_over_step": (facet_ms + gather_ms) / ms_step,
-                      "how": "profiling pass of K more steps: events before, between and after each step's "
-                             "two kernels (direct launches)"},
+                      "facet_in_step": ms_step * facet_ms / (facet_ms + gather_ms),
+                      "gather_in_step": ms_step * gather_ms / (facet_ms + gather_ms),
+                      "profiled_step_over_timed_step": (facet_ms + gather_ms) / ms_step,
+                      "how": "profiling pass of K more steps as launch pairs: events before, between and after "
+                             "each step's two kernels (direct launches), so facet + gather is that pass's step "
+                             "time; it exceeds the timed step by the launch gaps that graph replay or the "
+                             "persistent launch remove.  *_in_step: the timed step split in the profiled "
+                             "shares.  The rooflines use the profiled facet time (the slower, conservative one)"},
         "roofline": hbm_roofline(ref["facet_pass"] * F, fb, facet_ms, peak, peak_src,
                                  recorded_traffic(kern, name, prec),
                                  "%.0f B per facet-update (facet pass of a stored-frame layout)" % ref["facet_pass"]),
         "gather_roofline": hbm_roofline(gb, gb, gather_ms, peak, peak_src, None, "design bytes (no stored-layout "
                                                                                  "figure for the pass alone)"),
-        "step_roofline": hbm_roofline(ref["step"] * F, fb + gb, ms_step, peak, peak_src, None,
-                                      "%.0f B per facet-update (whole step of a stored-frame layout)" % ref["step"]),
+        "step_roofline": step_roofline(ref["step"] * F, fb + gb, ms_step, peak, peak_src),
         "energy_err_pct": float(energy[3]),
         "sizes": {"particles": N, "tets": T, "facets": F},
+        # kernels of ours launched in the timed region: two per step as launch pairs; as persistent
+        # launches one per ldpm_step call (one call per step when flushing, else one per 4096 steps)
+        "gpu_launches": 2 * steps if mode == 1 else (steps if flush is not None else -(-steps // 4096)),
     }
 
 
@@ -358,17 +422,24 @@ def run_ours(args, rank, world, local):
     if sampler:
         sampler.__enter__()
     mixed = run_leg(args.workload, wl, spec, bc, "mixed", args.steps, args.warmup, preroll, stream, flush, peak,
-                    peak_src, world)
+                    peak_src, world, args.launch)
     fp64 = run_leg(args.workload, wl, spec, bc, "fp64", max(3, args.steps // 4), args.warmup, preroll, stream, flush,
-                   peak, peak_src, world)
+                   peak, peak_src, world, args.launch)
     fp64["alu_roofline"] = fp64_alu_roofline(args.workload, fp64["kernel_ms"]["facet"])
     extra = {}
     if not args.no_extra and args.workload != "uniaxial_tension":
         # the 1.82M-facet uniaxial-tension cube beside the headline
         w2, s2, b2 = make_inputs("uniaxial_tension")
         extra["uniaxial_tension"] = run_leg("uniaxial_tension", w2, s2, b2, "mixed", args.steps, args.warmup,
-                                            w2.preroll, stream, flush, peak, peak_src, world)
+                                            w2.preroll, stream, flush, peak, peak_src, world, args.launch)
         del s2
+    if not args.no_extra and world == 1:
+        # launch pairs against one persistent launch per call, on the small (launch-bound), the 1.82M-facet
+        # and the 12.5M-facet specimens
+        extra["launch_modes"] = {n: mode_compare(n, p_, max(args.steps, 200) if n == "elastic_vibration" else args.steps,
+                                                 args.warmup, stream, flush)
+                                 for n, p_ in (("elastic_vibration", "fp64"), ("uniaxial_tension", "mixed"),
+                                               (args.workload, "mixed"))}
     if sampler:
         sampler.__exit__()
     clocks = sampler.summary() if sampler else None
@@ -396,7 +467,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": args.workload, "cube_mm": wl.edge, "d_min_mm": wl.d_min, "d_max_mm": wl.d_max,
                    "particles": N, "tets": T, "facets": F, "precision": "mixed: FP32 facet pass, FP64 particle state",
                    "dt_s": wl.dt, "l2": mixed["l2"], "timed_window": mixed["timed_window"],
-                   "launch_mode": mixed["launch_mode"],
+                   "launch": mixed["launch"],
                    "parallelism": "replicas" if world > 1 else "single GPU", "seed": wl.seed},
         "roofline": mixed["roofline"],
         "gather_roofline": mixed["gather_roofline"],
@@ -410,7 +481,7 @@ def run_ours(args, rank, world, local):
                 "d2h_bytes_per_step": d2h / K, "seconds": e2e_s,
                 "what": "ldpm_create from host arrays, K x (ldpm_step(1) + ldpm_energy read-back), "
                         "ldpm_get_state to host, ldpm_destroy"},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": mixed["gpu_launches"],
         "clocks": clocks,
     }
     res.update(extra)
@@ -485,9 +556,9 @@ def run_batch(args, rank, world, local):
                    "generation_s": round(gen_s, 1), "create_s": round(create_s, 1)},
         "roofline": hbm_roofline(ref["facet_pass"] * F, fb, facet_ms, peak, peak_src, None,
                                  "%.0f B per facet-update (facet pass of a stored-frame layout)" % ref["facet_pass"]),
-        "step_roofline": hbm_roofline(ref["step"] * F, fb + gb, tot / args.steps, peak, peak_src, None,
-                                      "%.0f B per facet-update (whole step of a stored-frame layout)" % ref["step"]),
-        "kernel_ms": {"facet": facet_ms, "gather": gather_ms, "sum_over_step": (facet_ms + gather_ms) / (tot / args.steps)},
+        "step_roofline": step_roofline(ref["step"] * F, fb + gb, tot / args.steps, peak, peak_src),
+        "kernel_ms": {"facet": facet_ms, "gather": gather_ms,
+                      "profiled_step_over_timed_step": (facet_ms + gather_ms) / (tot / args.steps)},
         "fp64_single_specimen": {"value": fp64_single, "facets": specs[0].n_facets},
         "batched_mixed_over_fp64_single": value / fp64_single,
         "max_energy_error_pct": max(errs),
@@ -898,7 +969,10 @@ def main():
                              "batched_unconfined_compression", "adjoint_uniaxial_tension"))
     ap.add_argument("--batch", type=int, default=64, help="specimens of the batched workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extra", action="store_true", help="skip the uniaxial-tension line beside the headline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the uniaxial-tension line and the launch-mode comparison beside the headline")
+    ap.add_argument("--launch", choices=("auto", "pairs", "persistent"), default="auto",
+                    help="launch mode of the timed legs: the library's autotuner (default) or a fixed one")
     ap.add_argument("--preroll", type=int, default=None,
                     help="untimed steps of the loading history before the warm-up (default: the workload's own, "
                          "enough for the loading wave to cross the specimen, so that the timed window sees every "
@@ -933,6 +1007,8 @@ def main():
         else:
             wl, spec, bc = make_inputs(args.workload)
             m = ldpm.Model(spec, wl.material, precision=args.ncu_case, dt=wl.dt or 2e-7, bc=bc, graph_chunk=-1)
+            if args.launch != "auto":
+                ldpm.ldpm_set_launch_mode(m.h, LAUNCH_MODES[args.launch])
             m.step(wl.preroll if args.preroll is None else args.preroll)
             m.sync()
             torch.cuda.profiler.start()

@@ -39,8 +39,10 @@ extern "C" {
 #define LDPM_E_CUDA (-3)          /* a CUDA call failed (message names it) */
 #define LDPM_E_OOM (-4)           /* device or host allocation failed */
 #define LDPM_E_UNSTABLE (-5)      /* a velocity or displacement became NaN/Inf (step too large?) */
-#define LDPM_E_TIMEOUT (-6)       /* reserved for a bounded device-side wait; no kernel waits today */
-#define LDPM_E_UNSUPPORTED (-7)   /* reserved; no call returns it today */
+#define LDPM_E_TIMEOUT (-6)       /* a grid barrier of the persistent step kernel waited longer than its
+                                     limit (ldpm_set_barrier_wait); the state is undefined until
+                                     ldpm_set_state or ldpm_load_checkpoint */
+#define LDPM_E_UNSUPPORTED (-7)   /* the persistent launch cannot be made co-resident on the device */
 
 typedef struct ldpm_ctx *ldpm_t; /* opaque handle, owned by the library */
 
@@ -143,9 +145,36 @@ int ldpm_create(const ldpm_geometry *geom, const ldpm_material *mat, const ldpm_
  * nsteps == 0 is a no-op.  Errors: INVALID_ARG (nsteps < 0), CUDA. */
 int ldpm_step(ldpm_t h, int64_t nsteps);
 
-/* Wait for all work enqueued on the handle's stream.  Returns UNSTABLE if a step produced a
- * non-finite velocity or displacement. */
+/* Wait for all work enqueued on the handle's stream.  Returns TIMEOUT if a grid barrier of the
+ * persistent step kernel gave up, UNSTABLE if a step produced a non-finite velocity or displacement. */
 int ldpm_sync(ldpm_t h);
+
+/* Launch modes of ldpm_step (a library service; both run the steps of Sec. 3 with the same device
+ * functions in the same order; each is deterministic, and the two agree to rounding, since the
+ * compiler may schedule and contract multiply-adds differently in the two kernels):
+ *   LDPM_LAUNCH_PAIRS       per step a facet-pass launch and a particle-pass launch, replayed from
+ *                           captured CUDA graphs (chunks of options.graph_chunk steps);
+ *   LDPM_LAUNCH_PERSISTENT  one cooperative launch per ldpm_step call (chunks of up to 4096 steps)
+ *                           running every step: facet pass, grid barrier, particle pass, grid
+ *                           barrier, with as many blocks as the device holds at once.  Each barrier
+ *                           wait is bounded; a wait that runs out ends the launch and the handle
+ *                           reports LDPM_E_TIMEOUT (see ldpm_set_barrier_wait).
+ * ldpm_create starts in LDPM_LAUNCH_PAIRS; with options.autotune = 1 it times both modes on the model
+ * and keeps the faster.  ldpm_set_launch_mode applies to steps enqueued afterwards.  Errors:
+ * INVALID_ARG, UNSUPPORTED (the persistent grid cannot be co-resident on this device). */
+#define LDPM_LAUNCH_PAIRS 1
+#define LDPM_LAUNCH_PERSISTENT 2
+int ldpm_set_launch_mode(ldpm_t h, int32_t mode);
+/* The handle's launch mode (LDPM_LAUNCH_*), or a negative error code. */
+int32_t ldpm_launch_mode(ldpm_t h);
+
+/* Bound of one grid-barrier wait of the persistent step kernel: `seconds` of the GPU's global timer
+ * (<= 0: 2 s, the default); a wait also gives up after 2^24 polls.  skip_block >= 0 is a
+ * fault-injection hook for tests of that bound: block `skip_block` of the next persistent launches
+ * does not arrive at the launch's first barrier, so every block's wait runs out and the call
+ * reports LDPM_E_TIMEOUT; -1 (the default) disables it.  No counterpart in the paper.  Errors:
+ * INVALID_ARG (seconds not finite or above 3600, skip_block < -1). */
+int ldpm_set_barrier_wait(ldpm_t h, double seconds, int32_t skip_block);
 
 /* Copy the state out (synchronises).  q, v: [N][6]; hist5: [F][5] per facet t_N, the tangential
  * traction t_M m + t_L l as a global 3-vector, e_max (the traction acting on facet_pi[k]); step: the
@@ -203,8 +232,9 @@ int ldpm_info(ldpm_t h, int64_t info[5], double *dt);
  * (no graph) with an event before the facet pass, one between the passes and one after the particle
  * pass, so the two kernel times of a step add up to its duration.  ldpm_profile_read fills ms[k]
  * (summed milliseconds) and count[k] (launches) for k = 0 kick, 1 facet pass, 2 gather+update,
- * 3 reverse facet pass and 4 reverse particle pass (ldpm_adjoint); n = entries the caller provides
- * (at most 5 are written). */
+ * 3 reverse facet pass, 4 reverse particle pass (ldpm_adjoint) and 5 persistent step launch (whole
+ * launches: the persistent kernel has no per-pass split); n = entries the caller provides (at most 6
+ * are written). */
 int ldpm_profile(ldpm_t h, int32_t enable);
 int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n);
 

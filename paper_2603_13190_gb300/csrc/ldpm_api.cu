@@ -221,8 +221,11 @@ struct ldpm_ctx {
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
     std::vector<std::array<int, 3>> ev_pairs;  // (kernel id, event index of start, event index of end)
-    double prof_ms[5] = {0, 0, 0, 0, 0};  // kick, facet pass, particle pass, reverse facet, reverse particle
-    int64_t prof_cnt[5] = {0, 0, 0, 0, 0};
+    double prof_ms[6] = {0, 0, 0, 0, 0, 0};  // kick, facet pass, particle pass, reverse facet, reverse particle,
+    int64_t prof_cnt[6] = {0, 0, 0, 0, 0, 0};  // persistent step launch
+    int launch_mode = LDPM_LAUNCH_PAIRS;
+    PersistCtl pctl;          // device words arrive / status of the persistent kernel's grid barriers
+    int persist_grid = 0;     // its grid (co-resident blocks), 0 until the mode is first chosen
     size_t rsize() const { return prec == LDPM_MIXED ? sizeof(float) : sizeof(double); }
     size_t r4size() const { return 4 * rsize(); }
 };
@@ -238,7 +241,7 @@ void free_model(ldpm_ctx *h)
                     h->dm.geo,
                     h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
                     h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch, h->d_ticket,
-                    h->d_pmap};
+                    h->d_pmap, h->pctl.arrive, h->pctl.status};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->h_out16) cudaFreeHost(h->h_out16);
@@ -730,10 +733,13 @@ int estimate_dt(ldpm_ctx *h, std::vector<double> &lam)
 
 int kick(ldpm_ctx *h);
 int enqueue_direct(ldpm_ctx *h, int64_t nsteps);
+int enqueue_steps(ldpm_ctx *h, int64_t nsteps);
+int set_launch_mode(ldpm_ctx *h, int mode);
 
 // Launch-shape autotuner: times each candidate (tetrahedra per facet-pass block x lanes per particle)
 // on the model itself for a few steps, restoring the complete mutable state after every trial, and
-// keeps the fastest.  Results stay deterministic for the chosen shape: the facet-pass shape does not
+// keeps the fastest; then times that shape's graph-replayed launch pairs against the persistent launch
+// the same way and keeps the faster mode.  Results stay deterministic for the chosen shape: the facet-pass shape does not
 // change any arithmetic, the lanes per particle change the order of a particle's sums (rounding-level
 // differences between shapes).
 int autotune(ldpm_ctx *h)
@@ -783,6 +789,30 @@ int autotune(ldpm_ctx *h)
         }
     dm.tets_per_block = bt;
     dm.gather_lanes = bl;
+    // launch mode: the chosen launch pairs replayed from CUDA graphs against the persistent launch, each
+    // timed over the same steps from the same state (a warm-up call first captures the graphs)
+    float t_mode[3] = {0.f, 0.f, 0.f};
+    for (int mode = LDPM_LAUNCH_PAIRS; mode <= LDPM_LAUNCH_PERSISTENT && e == cudaSuccess && rc == 0; ++mode) {
+        if (set_launch_mode(h, mode) != LDPM_OK) {  // no co-resident persistent grid: pairs only
+            set_last_error("");
+            t_mode[mode] = 1e30f;
+            continue;
+        }
+        for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+        h->graphs.clear();
+        constexpr int kTrial = 8;
+        if ((rc = enqueue_steps(h, kTrial))) break;
+        e = cudaEventRecord(a, h->stream);
+        if (e == cudaSuccess && !(rc = enqueue_steps(h, kTrial))) e = cudaEventRecord(b, h->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t_mode[mode], a, b);
+        if (e == cudaSuccess) e = save(false);
+    }
+    for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+    if (rc == 0 && e == cudaSuccess)
+        rc = set_launch_mode(h, t_mode[LDPM_LAUNCH_PERSISTENT] < t_mode[LDPM_LAUNCH_PAIRS] ? LDPM_LAUNCH_PERSISTENT
+                                                                                         : LDPM_LAUNCH_PAIRS);
     cudaError_t e2 = cudaStreamSynchronize(h->stream);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
@@ -933,8 +963,11 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
         (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())) ||
-        (rc = dalloc(&h->d_ticket, 1)) || (rc = dalloc(&h->d_pmap, (size_t)N)))
+        (rc = dalloc(&h->d_ticket, 1)) || (rc = dalloc(&h->d_pmap, (size_t)N)) ||
+        (rc = dalloc(&h->pctl.arrive, 1)) || (rc = dalloc(&h->pctl.status, 1)))
         return rc;
+    CU(cudaMemset(h->pctl.arrive, 0, sizeof(unsigned)));
+    CU(cudaMemset(h->pctl.status, 0, sizeof(int32_t)));
     {
         std::vector<int32_t> pmap((size_t)N);
         size_t base = 0;
@@ -1076,6 +1109,69 @@ int collect_profile(ldpm_ctx *h)
     return LDPM_OK;
 }
 
+// Persistent launches of nsteps steps, in chunks of at most 4096 steps (each launch then stays short,
+// and the barrier counter, 2 x grid per step, within 32 bits); while profiling each launch is
+// bracketed by events (kernel id 5).
+int enqueue_persistent(ldpm_ctx *h, int64_t nsteps)
+{
+    const int64_t grid = std::max(1, h->persist_grid);
+    const int64_t cap = std::min<int64_t>(4096, (int64_t)(0xffffffffu / (2 * grid)) - 1);
+    for (int64_t left = nsteps; left > 0;) {
+        const int64_t len = std::min(left, cap);
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (h->prof) {
+            if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess)
+                return fail(LDPM_E_CUDA, "event create failed");
+            h->ev_pool.push_back(a);
+            h->ev_pool.push_back(b);
+            h->ev_pairs.push_back({5, (int)h->ev_pool.size() - 2, (int)h->ev_pool.size() - 1});
+            CU(cudaEventRecord(a, h->stream));
+        }
+        int grid_used = 0;
+        cudaError_t e = h->prec == LDPM_MIXED ? launch_persistent<float>(h->dm, len, h->pctl, &grid_used, h->stream)
+                                              : launch_persistent<double>(h->dm, len, h->pctl, &grid_used, h->stream);
+        if (e != cudaSuccess) return fail(LDPM_E_CUDA, "persistent step launch: %s", cudaGetErrorString(e));
+        if (h->prof) CU(cudaEventRecord(b, h->stream));
+        left -= len;
+    }
+    return LDPM_OK;
+}
+
+// nsteps steps in the handle's launch mode: persistent launches, or launch pairs replayed from CUDA
+// graphs captured per chunk length (direct launches while profiling or with graph_chunk < 0).
+int enqueue_steps(ldpm_ctx *h, int64_t nsteps)
+{
+    if (h->launch_mode == LDPM_LAUNCH_PERSISTENT) return enqueue_persistent(h, nsteps);
+    if (h->prof) return enqueue_profiled(h, nsteps);
+    if (h->graph_chunk < 0) return enqueue_direct(h, nsteps);
+    int rc;
+    const int64_t chunk = std::max(1, h->graph_chunk);
+    for (int64_t left = nsteps; left > 0;) {
+        const int64_t len = std::min(left, chunk);
+        cudaGraphExec_t ex;
+        if ((rc = graph_for(h, len, &ex))) return rc;
+        CU(cudaGraphLaunch(ex, h->stream));
+        left -= len;
+    }
+    return LDPM_OK;
+}
+
+// Choose the launch mode; the persistent one needs its grid to be co-resident on the device.
+int set_launch_mode(ldpm_ctx *h, int mode)
+{
+    if (mode == LDPM_LAUNCH_PERSISTENT) {
+        int grid = 0;
+        cudaError_t e = h->prec == LDPM_MIXED ? launch_persistent<float>(h->dm, 0, h->pctl, &grid, h->stream)
+                                              : launch_persistent<double>(h->dm, 0, h->pctl, &grid, h->stream);
+        if (e != cudaSuccess || grid < 1)
+            return fail(LDPM_E_UNSUPPORTED, "persistent launch not possible on this device: %s",
+                        cudaGetErrorString(e));
+        h->persist_grid = grid;
+    }
+    h->launch_mode = mode;
+    return LDPM_OK;
+}
+
 // Run `launch`; while profiling, bracket it with events on the stream (kernel id kid).
 template <class Fn>
 int timed(ldpm_ctx *h, int kid, Fn &&launch)
@@ -1096,9 +1192,14 @@ int timed(ldpm_ctx *h, int kid, Fn &&launch)
 
 int check_flag(ldpm_ctx *h)
 {
-    int32_t fl = 0;
+    int32_t fl = 0, st = 0;
     CU(cudaMemcpyAsync(&fl, h->dm.flag, sizeof(fl), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(&st, h->pctl.status, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    if (st)
+        return fail(LDPM_E_TIMEOUT, "a grid barrier of the persistent step kernel waited longer than %.3g s; the "
+                    "state is undefined until ldpm_set_state or ldpm_load_checkpoint",
+                    1e-9 * (double)h->pctl.wait_ns);
     if (fl) return fail(LDPM_E_UNSTABLE, "non-finite velocity or displacement (time step too large?)");
     return LDPM_OK;
 }
@@ -1372,22 +1473,37 @@ int ldpm_step(ldpm_t h, int64_t nsteps)
     if (nsteps == 0) return LDPM_OK;
     DevGuard dg(h->device);
     try {
-        if (h->prof) return enqueue_profiled(h, nsteps);
-        if (h->graph_chunk < 0) return enqueue_direct(h, nsteps);
-        int rc;
-        int64_t left = nsteps;
-        const int64_t chunk = std::max(1, h->graph_chunk);
-        while (left > 0) {
-            const int64_t len = std::min(left, chunk);
-            cudaGraphExec_t ex;
-            if ((rc = graph_for(h, len, &ex))) return rc;
-            CU(cudaGraphLaunch(ex, h->stream));
-            left -= len;
-        }
-        return LDPM_OK;
+        return enqueue_steps(h, nsteps);
     } catch (...) {
         return fail(LDPM_E_CUDA, "unexpected exception in ldpm_step");
     }
+}
+
+int ldpm_set_launch_mode(ldpm_t h, int32_t mode)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    if (mode != LDPM_LAUNCH_PAIRS && mode != LDPM_LAUNCH_PERSISTENT)
+        return fail(LDPM_E_INVALID_ARG, "mode must be LDPM_LAUNCH_PAIRS or LDPM_LAUNCH_PERSISTENT");
+    DevGuard dg(h->device);
+    return set_launch_mode(h, mode);
+}
+
+int32_t ldpm_launch_mode(ldpm_t h)
+{
+    g_err.clear();
+    if (!h) return fail(LDPM_E_INVALID_ARG, "bad handle");
+    return h->launch_mode;
+}
+
+int ldpm_set_barrier_wait(ldpm_t h, double seconds, int32_t skip_block)
+{
+    g_err.clear();
+    if (!h || !std::isfinite(seconds) || seconds > 3600.0 || skip_block < -1)
+        return fail(LDPM_E_INVALID_ARG, "bad handle, seconds not finite or above 3600, or skip_block < -1");
+    h->pctl.wait_ns = seconds > 0 ? (uint64_t)(seconds * 1e9) : 2000000000ull;
+    h->pctl.skip_block = skip_block;
+    return LDPM_OK;
 }
 
 int ldpm_sync(ldpm_t h)
@@ -1516,6 +1632,7 @@ int ldpm_set_state(ldpm_t h, const double *q, const double *v, const double *his
             return fail(LDPM_E_CUDA, "history upload: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
         CU(cudaMemcpy(h->dm.step, &step, sizeof(step), cudaMemcpyHostToDevice));
         CU(cudaMemset(h->dm.flag, 0, sizeof(int32_t)));
+        CU(cudaMemset(h->pctl.status, 0, sizeof(int32_t)));
         if ((rc = forces_from_history(h))) return rc;
         if ((rc = kick(h))) return rc;
         CU(cudaStreamSynchronize(h->stream));
@@ -1711,7 +1828,7 @@ int ldpm_profile(ldpm_t h, int32_t enable)
     DevGuard dg(h->device);
     if (h->prof) collect_profile(h);
     h->prof = enable != 0;
-    for (int k = 0; k < 5; ++k) {
+    for (int k = 0; k < 6; ++k) {
         h->prof_ms[k] = 0;
         h->prof_cnt[k] = 0;
     }
@@ -1725,7 +1842,7 @@ int ldpm_profile_read(ldpm_t h, double *ms, int64_t *count, int32_t n)
     DevGuard dg(h->device);
     int rc = collect_profile(h);
     if (rc) return rc;
-    for (int k = 0; k < n && k < 5; ++k) {
+    for (int k = 0; k < n && k < 6; ++k) {
         if (ms) ms[k] = h->prof_ms[k];
         if (count) count[k] = h->prof_cnt[k];
     }
@@ -1779,6 +1896,7 @@ int ldpm_load_checkpoint(ldpm_t h, const void *buf)
     std::memcpy(&fl64, q + 8, 8);
     int32_t fl = (int32_t)fl64;
     CU(cudaMemcpy(h->dm.flag, &fl, 4, cudaMemcpyHostToDevice));
+    CU(cudaMemset(h->pctl.status, 0, sizeof(int32_t)));
     for (size_t s = 0; s < h->sp.size(); ++s) std::memcpy(&h->sp[s].W_kin0, q + 16 + 8 * s, 8);
     CU(launch_mirror(h->dm, h->stream));
     CU(cudaStreamSynchronize(h->stream));

@@ -98,6 +98,19 @@ struct DeviceModel {
     int32_t *flag = nullptr;        // non-finite state seen
 };
 
+// Control block of the persistent step kernel.  `arrive` counts the blocks' arrivals at the grid
+// barriers of one launch (zeroed before the launch); `status` is 0, or kStatusTimeout once a barrier
+// wait gave up (it stays set: later persistent launches return at once, and the handle reports
+// LDPM_E_TIMEOUT until its state is replaced); `wait_ns` bounds one barrier wait; block `skip_block`
+// (-1: none) does not arrive at the first barrier of the launch (fault injection for tests).
+constexpr int32_t kStatusTimeout = 1;
+struct PersistCtl {
+    unsigned *arrive = nullptr;
+    int32_t *status = nullptr;
+    uint64_t wait_ns = 2000000000ull;
+    int32_t skip_block = -1;
+};
+
 // Reverse (adjoint) pass workspace (ldpm_adjoint.cu).  The objective is
 //   J = sum_n sum_i c_i f_i(t_n),  c = -seed / K on constrained DOFs, 0 elsewhere
 // (the time mean of the seeded reactions R = m a - f), and its gradient with respect to the
@@ -132,6 +145,13 @@ cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s);
 // q, v [n][6] device arrays (either may be null).
 cudaError_t launch_state_to_user(const DeviceModel &m, const int32_t *pmap, int64_t n, double *q, double *v,
                                  cudaStream_t s);
+// One cooperative launch of `nsteps` steps of the persistent step kernel (mixed or FP64 by R).  The grid
+// is the number of co-resident blocks (occupancy x SMs), written to *grid_out; nsteps = 0 only
+// computes it.  Returns the launch error (cudaErrorCooperativeLaunchTooLarge if the grid cannot be
+// resident).
+template <class R>
+cudaError_t launch_persistent(const DeviceModel &m, int64_t nsteps, const PersistCtl &ctl, int *grid_out,
+                              cudaStream_t s);
 // `src_override` replaces the particle records the facet pass reads (FP64 mode: pstate layout;
 // mixed mode: pm32 layout); null = the model's own.
 template <class R>

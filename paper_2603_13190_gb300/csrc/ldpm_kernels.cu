@@ -51,10 +51,35 @@ struct Stride {
     static constexpr int con = sizeof(R) == 4 ? 12 : 14;
 };
 
+// Loads of data that the persistent step kernel writes during its own launch (particle records,
+// history, vertex shares, the step counter).  With PERSIST they are explicit weak global loads
+// (ld.global.ca): never the read-only non-coherent path a compiler may pick for const __restrict__
+// pointers, which is valid only for data that no thread writes during the launch.  Values written
+// by other blocks become visible through the grid barrier's fences.
+template <bool PERSIST, class T>
+__device__ __forceinline__ T ld_live(const T *p)
+{
+    if constexpr (PERSIST)
+        return __ldca(p);
+    else
+        return *p;
+}
+template <bool PERSIST>
+__device__ __forceinline__ double4a ld_live(const double4a *p)
+{
+    if constexpr (PERSIST) {
+        const double2 a = __ldca(reinterpret_cast<const double2 *>(p));
+        const double2 b = __ldca(reinterpret_cast<const double2 *>(p) + 1);
+        return double4a{a.x, a.y, b.x, b.y};
+    } else {
+        return *p;
+    }
+}
+
 // Staging of one tetrahedron vertex (lane4 = 4 * tetrahedron + vertex within the tile; all 32 lanes
 // of the warp take part, the shuffles stay within each tetrahedron's 4 lanes): the particle record,
 // differences to the tetrahedron's vertex 0 into shared row sv[lane4], and e_V of the tetrahedron.
-template <class R, int MODE>
+template <class R, int MODE, bool PERSIST = false>
 __device__ __forceinline__ void stage_vertex(const DeviceModel &m, const void *__restrict__ vsrc, int64_t tet0,
                                              int lane4, R (*sv)[Stride<R>::row], R *seV, int *sok)
 {
@@ -76,7 +101,7 @@ __device__ __forceinline__ void stage_vertex(const DeviceModel &m, const void *_
             const float4 *r4 = reinterpret_cast<const float4 *>(src + kMirror * (int64_t)p);
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-                const float4 w = r4[k];
+                const float4 w = ld_live<PERSIST>(r4 + k);
                 rec[4 * k] = w.x;
                 rec[4 * k + 1] = w.y;
                 rec[4 * k + 2] = w.z;
@@ -107,7 +132,7 @@ __device__ __forceinline__ void stage_vertex(const DeviceModel &m, const void *_
             const double2 *r2 = reinterpret_cast<const double2 *>(src + 16 * (int64_t)p);
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-                const double2 w = r2[k];
+                const double2 w = ld_live<PERSIST>(r2 + k);
                 rec[2 * k] = w.x;
                 rec[2 * k + 1] = w.y;
             }
@@ -374,28 +399,16 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 // GB300 in the loaded state of 1.82M facets: 43.1 us against 45.2 us).
 constexpr int kTileTets = 8;
 constexpr int kPlane = 6 * 4 * kTileTets + 2;
-template <class R, int MODE, int WPB, bool PF, bool S1>
-__global__ void __launch_bounds__(32 * WPB)
-    facet_warp_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc)
+// One 8-tetrahedron tile of the facet pass, run by one warp on its own shared rows: phases A-C below.
+// PERSIST: called from the persistent step kernel (live data through ld_live).
+template <class R, int MODE, bool PF, bool S1, bool PERSIST>
+__device__ __forceinline__ void facet_tile(const DeviceModel &m, const void *__restrict__ vsrc, int64_t tet0,
+                                           int lane, R (*sv)[Stride<R>::row], R *spl, R *seV, int *sok)
 {
     using T4 = R4<R>;
     using V2 = typename VecT<R>::v2;
-    constexpr int TETS = kTileTets;
-    __shared__ alignas(16) R sv_[WPB][TETS * 4][Stride<R>::row];
-    __shared__ alignas(16) R spl_[WPB][6 * kPlane];
-    __shared__ R seV_[WPB][TETS];
-    __shared__ int sok_[WPB][TETS];
     const T4 *__restrict__ geo = static_cast<const T4 *>(m.geo);
-    const T4 *__restrict__ hist = static_cast<const T4 *>(m.hist);
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    R(*sv)[Stride<R>::row] = sv_[w];
-    R *spl = spl_[w];
-    R *seV = seV_[w];
-    int *sok = sok_[w];
-    const int64_t tet0 = ((int64_t)blockIdx.x * WPB + w) * TETS;
-    if (MODE == FACET_STEP && blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
-    if (tet0 >= m.T) return;  // whole warp (T is a multiple of the tile)
-
+    const T4 *hist = static_cast<const T4 *>(m.hist);
     // ---- prefetch the lane's three facets
     T4 g[3] = {}, h[3] = {}, pp[3] = {};
 #pragma unroll
@@ -404,12 +417,12 @@ __global__ void __launch_bounds__(32 * WPB)
         const int64_t f = tet0 * 12 + fi;
         if (tet0 + fi / 12 < m.T) {
             g[i] = geo[f];
-            if (MODE != FACET_ELASTIC) h[i] = hist[f];
+            if (MODE != FACET_ELASTIC) h[i] = ld_live<PERSIST>(hist + f);
             if (PF) pp[i] = static_cast<const T4 *>(m.pf)[f];
         }
     }
     // ---- phase A
-    stage_vertex<R, MODE>(m, vsrc, tet0, lane, sv, seV, sok);
+    stage_vertex<R, MODE, PERSIST>(m, vsrc, tet0, lane, sv, seV, sok);
     __syncwarp();
     // ---- phase B
 #pragma unroll
@@ -455,6 +468,23 @@ __global__ void __launch_bounds__(32 * WPB)
             }
         }
     }
+    __syncwarp();  // the warp's shared rows may be reused for another tile
+}
+
+template <class R, int MODE, int WPB, bool PF, bool S1>
+__global__ void __launch_bounds__(32 * WPB)
+    facet_warp_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc)
+{
+    constexpr int TETS = kTileTets;
+    __shared__ alignas(16) R sv_[WPB][TETS * 4][Stride<R>::row];
+    __shared__ alignas(16) R spl_[WPB][6 * kPlane];
+    __shared__ R seV_[WPB][TETS];
+    __shared__ int sok_[WPB][TETS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tet0 = ((int64_t)blockIdx.x * WPB + w) * TETS;
+    if (MODE == FACET_STEP && blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
+    if (tet0 >= m.T) return;  // whole warp (T is a multiple of the tile)
+    facet_tile<R, MODE, PF, S1, false>(m, vsrc, tet0, lane, sv_[w], spl_[w], seV_[w], sok_[w]);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -472,17 +502,16 @@ __global__ void __launch_bounds__(32 * WPB)
 // ~64 cycles per sub-partition, so the compensated sums run on the FP32 pipe; FP32 <-> FP64
 // conversions are integer operations.
 // ------------------------------------------------------------------------------------------------
-template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+// One group of LPP lanes, particle p (all 32 lanes of the warp take part in its shuffles).
+template <class R, int MODE, int LPP, bool PERSIST>
+__device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, int lane, double *__restrict__ out6)
 {
     static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per particle");
     constexpr bool kMixed = sizeof(R) == 4;
     using Acc = typename std::conditional<kMixed, ff, double>::type;
     const int32_t *__restrict__ ent = static_cast<const int32_t *>(m.ent);
-    const R *__restrict__ tvc = static_cast<const R *>(m.tvc);
-    const int lane = threadIdx.x & 31;
+    const R *tvc = static_cast<const R *>(m.tvc);
     const int sub = lane & (LPP - 1);
-    const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
     const bool valid = p < m.N;
     // lanes 0, 1, 2, 4, 5, 6 of the group own DOFs 0..5 (where halving_sum6 leaves their sums); the
     // other lanes mirror DOF 0 and store nothing
@@ -526,9 +555,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(Dev
             for (int k = 0; k < kSlots; ++k)
                 if (id[k] >= 0) {
                     const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)id[k]);
-                    w[k][0] = src[0];
-                    w[k][1] = src[1];
-                    w[k][2] = src[2];
+                    w[k][0] = ld_live<PERSIST>(src);
+                    w[k][1] = ld_live<PERSIST>(src + 1);
+                    w[k][2] = ld_live<PERSIST>(src + 2);
                 }
 #pragma unroll
             for (int k = 0; k < kSlots; ++k)
@@ -545,9 +574,9 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(Dev
             for (int k = 0; k < kSlots; ++k)
                 if (id[k] >= 0) {
                     const double2 *src = reinterpret_cast<const double2 *>(tvc + 6 * (int64_t)id[k]);
-                    w[k][0] = src[0];
-                    w[k][1] = src[1];
-                    w[k][2] = src[2];
+                    w[k][0] = ld_live<PERSIST>(src);
+                    w[k][1] = ld_live<PERSIST>(src + 1);
+                    w[k][2] = ld_live<PERSIST>(src + 2);
                 }
 #pragma unroll
             for (int k = 0; k < kSlots; ++k)
@@ -586,7 +615,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(Dev
     // vb (ramp(t +- dt/2) differences) / dt, so their sum telescopes to vb (r(t1+dt/2) - r(t0-dt/2)) / dt
     double g_bc = 0.0, v_bc = 0.0;
     if (mask > 1) {
-        const int64_t n1 = *m.step;
+        const int64_t n1 = ld_live<PERSIST>(reinterpret_cast<const long long *>(m.step));
         const double t1 = (double)n1 * dt;
         const double r_next = ramp(t1 + hdt, S.inv_ramp);
         g_bc = m.bc_vm[6 * pc_ + d] * (r_next - ramp(t1 - dt - hdt, S.inv_ramp)) * S.inv_dt;
@@ -660,6 +689,123 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(Dev
             if (need_we) pd[7] += dWe_acc;
         }
     }
+}
+
+template <class R, int MODE, int LPP>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 5 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
+    gather_group<R, MODE, LPP, false>(m, p, lane, out6);
+}
+
+// ------------------------------------------------------------------------------------------------
+// Persistent step kernel: one cooperative launch runs `nsteps` whole steps.  Each step is the facet
+// pass (warps take 8-tetrahedron tiles in a grid-stride loop), a grid barrier, the particle pass (warps
+// take groups of 4 particles), and a second grid barrier; the arithmetic and summation orders are
+// those of facet_warp_kernel and gather_kernel<.., 8>, so results equal the launch-pair path bit for
+// bit.  The cooperative launch guarantees that all blocks are resident, so every barrier completes
+// unless a block fails to arrive; each wait is nevertheless bounded (PersistCtl::wait_ns of
+// %globaltimer and kMaxPolls polls), after which the block sets the status word and returns, and
+// every other block stops at its next wait.
+// ------------------------------------------------------------------------------------------------
+constexpr uint32_t kMaxPolls = 1u << 24;
+
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Strong relaxed load at GPU scope: served by L2, and, unlike an acquire, it does not invalidate the
+// SM's L1 at every poll (which would cost the blocks still working on that SM their cached lines).
+__device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Barrier `target / gridDim.x` of the launch: all blocks' writes before it are visible to all blocks
+// after it.  Thread 0 of the block releases the block's writes (fence, then a relaxed atomic arrival;
+// with `arrive` false, the fault-injection hook, it does not arrive) and polls the arrival count with
+// relaxed loads, sleeping 32 to 256 ns between polls, until it reaches `target`; one fence after the
+// last poll then acquires the other blocks' writes (a relaxed read followed by a fence is an acquire
+// in the PTX memory model).  Returns false in every thread of the block if the wait gave up: its own
+// limit was reached (the status word is set), or another block had set the status.
+__device__ __forceinline__ bool grid_barrier(const PersistCtl &c, unsigned target, bool arrive)
+{
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        if (arrive) atomicAdd(c.arrive, 1u);
+        const uint64_t t0 = global_ns();
+        unsigned nap = 32;
+        for (uint32_t it = 0;; ++it) {
+            if (ld_relaxed_gpu(c.arrive) >= target) break;
+            if (*(volatile const int32_t *)c.status != 0) {
+                ok = 0;
+                break;
+            }
+            if (it >= kMaxPolls || global_ns() - t0 > c.wait_ns) {
+                atomicCAS(c.status, 0, kStatusTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(nap);
+            nap = nap < 256 ? 2 * nap : 256;
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+template <class R, bool PF, bool S1, int WPB>
+__global__ void __launch_bounds__(32 * WPB)
+    step_persistent_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc, int64_t nsteps,
+                           PersistCtl ctl)
+{
+    constexpr int TETS = kTileTets;
+    __shared__ alignas(16) R sv_[WPB][TETS * 4][Stride<R>::row];
+    __shared__ alignas(16) R spl_[WPB][6 * kPlane];
+    __shared__ R seV_[WPB][TETS];
+    __shared__ int sok_[WPB][TETS];
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) s_stop = *(volatile const int32_t *)ctl.status;
+    __syncthreads();
+    if (s_stop != 0) return;  // an earlier launch gave up: no work (the whole block)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * WPB + w, nw = (int64_t)gridDim.x * WPB;
+    const int64_t tiles = m.T / TETS;             // T is a multiple of the tile
+    const int64_t groups = ((int64_t)m.N + 3) / 4;  // 4 particles of 8 lanes per warp
+    unsigned target = 0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
+        for (int64_t t = gw; t < tiles; t += nw)
+            facet_tile<R, FACET_STEP, PF, S1, true>(m, vsrc, t * TETS, lane, sv_[w], spl_[w], seV_[w], sok_[w]);
+        target += gridDim.x;
+        if (!grid_barrier(ctl, target, !(n == 0 && (int)blockIdx.x == ctl.skip_block))) return;
+        for (int64_t g = gw; g < groups; g += nw) gather_group<R, GATHER_STEP_MID, 8, true>(m, 4 * g + lane / 8, lane, nullptr);
+        target += gridDim.x;
+        if (!grid_barrier(ctl, target, true)) return;
+    }
+}
+
+template <class R, bool PF, bool S1>
+constexpr int persist_wpb()
+{
+    return sizeof(R) == 4 ? 4 : 2;  // static shared memory stays below 48 KB per block
+}
+
+template <class R, bool PF, bool S1>
+const void *persist_fn()
+{
+    return reinterpret_cast<const void *>(&step_persistent_kernel<R, PF, S1, persist_wpb<R, PF, S1>()>);
 }
 
 // First half kick and drift of a stepping call: v_{n+1/2} = v_n + dt/2 a_n, q_{n+1} = q_n + dt v_{n+1/2}.
@@ -977,6 +1123,38 @@ cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t
     return launch_facet_pf<R, MODE, false>(m, pst, s);
 }
 
+// Persistent launch of `nsteps` steps (cooperative; grid = resident blocks per SM x SMs).  Returns
+// cudaErrorCooperativeLaunchTooLarge (or another launch error) if the grid cannot be co-resident.
+template <class R>
+cudaError_t launch_persistent_r(const DeviceModel &m, int64_t nsteps, const PersistCtl &ctl, int *grid_out,
+                                cudaStream_t s)
+{
+    const void *fn = (sizeof(R) == 4 && m.n_spec == 1) ? (m.pf ? persist_fn<R, true, true>() : persist_fn<R, false, true>())
+                                                        : (m.pf ? persist_fn<R, true, false>() : persist_fn<R, false, false>());
+    const int threads = 32 * (sizeof(R) == 4 ? 4 : 2);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    // as many blocks as the device holds at once, but no more than the work needs: every block takes
+    // part in every barrier, so idle blocks on a small specimen would only slow the barriers down
+    const int wpb = threads / 32;
+    const int64_t units = std::max<int64_t>(m.T / kTileTets, ((int64_t)m.N + 3) / 4);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, (units + wpb - 1) / wpb));
+    if (grid_out) *grid_out = (int)grid;
+    if (nsteps <= 0) return cudaSuccess;
+    const void *vsrc = sizeof(R) == 4 ? static_cast<const void *>(m.pm32) : static_cast<const void *>(m.pstate);
+    DeviceModel mm = m;
+    int64_t ns = nsteps;
+    PersistCtl c = ctl;
+    void *args[] = {&mm, &vsrc, &ns, &c};
+    e = cudaMemsetAsync(ctl.arrive, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(threads), args, 0, s);
+}
+
 }  // namespace
 
 cudaError_t launch_unkick(const DeviceModel &m, double *out12, cudaStream_t s)
@@ -1092,6 +1270,15 @@ cudaError_t launch_hist_from_user(const DeviceModel &m, const double *in5, cudaS
     return cudaGetLastError();
 }
 
+template <class R>
+cudaError_t launch_persistent(const DeviceModel &m, int64_t nsteps, const PersistCtl &ctl, int *grid_out,
+                              cudaStream_t s)
+{
+    return launch_persistent_r<R>(m, nsteps, ctl, grid_out, s);
+}
+
+template cudaError_t launch_persistent<float>(const DeviceModel &, int64_t, const PersistCtl &, int *, cudaStream_t);
+template cudaError_t launch_persistent<double>(const DeviceModel &, int64_t, const PersistCtl &, int *, cudaStream_t);
 template cudaError_t launch_facet<float>(const DeviceModel &, int, const void *, cudaStream_t);
 template cudaError_t launch_facet<double>(const DeviceModel &, int, const void *, cudaStream_t);
 template cudaError_t launch_gather<float>(const DeviceModel &, int, double *, cudaStream_t);

@@ -66,6 +66,9 @@ def signatures():
         "ldpm_create": ([P, P, P, P], C.c_int),
         "ldpm_step": ([P, I64], C.c_int),
         "ldpm_sync": ([P], C.c_int),
+        "ldpm_set_launch_mode": ([P, I32], C.c_int),
+        "ldpm_launch_mode": ([P], I32),
+        "ldpm_set_barrier_wait": ([P, D, I32], C.c_int),
         "ldpm_get_state": ([P, P, P, P, P], C.c_int),
         "ldpm_get_state_device": ([P, P, P, P, P], C.c_int),
         "ldpm_set_state": ([P, P, P, P, I64], C.c_int),
@@ -247,6 +250,24 @@ def ldpm_step(h, nsteps: int) -> None:
     _check(lib().ldpm_step(h, int(nsteps)), "ldpm_step")
 
 
+LDPM_LAUNCH_PAIRS, LDPM_LAUNCH_PERSISTENT = 1, 2
+
+
+def ldpm_set_launch_mode(h, mode: int) -> None:
+    _check(lib().ldpm_set_launch_mode(h, int(mode)), "ldpm_set_launch_mode")
+
+
+def ldpm_launch_mode(h) -> int:
+    r = lib().ldpm_launch_mode(h)
+    if r < 0:
+        _check(r, "ldpm_launch_mode")
+    return int(r)
+
+
+def ldpm_set_barrier_wait(h, seconds: float, skip_block: int = -1) -> None:
+    _check(lib().ldpm_set_barrier_wait(h, float(seconds), int(skip_block)), "ldpm_set_barrier_wait")
+
+
 def ldpm_sync(h) -> None:
     _check(lib().ldpm_sync(h), "ldpm_sync")
 
@@ -313,10 +334,10 @@ def ldpm_profile(h, enable: bool) -> None:
 
 def ldpm_profile_read(h):
     """Summed milliseconds and launch counts: kick, facet pass, particle pass, reverse facet pass,
-    reverse particle pass."""
-    ms = np.zeros(5)
-    cnt = np.zeros(5, np.int64)
-    _check(lib().ldpm_profile_read(h, _ptr(ms), _ptr(cnt), 5), "ldpm_profile_read")
+    reverse particle pass, persistent step launch."""
+    ms = np.zeros(6)
+    cnt = np.zeros(6, np.int64)
+    _check(lib().ldpm_profile_read(h, _ptr(ms), _ptr(cnt), 6), "ldpm_profile_read")
     return ms, cnt
 
 

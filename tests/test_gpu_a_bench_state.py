@@ -67,7 +67,10 @@ def test_fp64_trajectory_reaches_the_bench_state(bench_state):
     e, r = m.energy()
     assert_elementwise(e[:3], b["e0"][:3], 1e-9, "energies")
     assert_elementwise(r, b["r0"], 1e-9, "reactions")
-    assert np.abs(ho[:, 0]).max() > 0.1 * b["wl"].material["sigma_t"], "the state must be loaded"
+    # the loading wave has crossed the specimen: every facet carries traction (the timed window does
+    # not run on the law's zero-strain path), both branches of the law are in use
+    assert np.mean(np.abs(ho[:, 0]) > 0) > 0.99, "the loading wave must have crossed the specimen"
+    assert np.any(ho[:, 0] > 0) and np.any(ho[:, 0] < 0)
     m.close()
 
 
