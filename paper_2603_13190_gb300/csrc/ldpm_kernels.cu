@@ -728,22 +728,22 @@ __device__ __forceinline__ unsigned ld_relaxed_gpu(const unsigned *p)
 }
 
 // Barrier `target / gridDim.x` of the launch: all blocks' writes before it are visible to all blocks
-// after it.  Thread 0 of the block releases the block's writes (fence, then a relaxed atomic arrival;
-// with `arrive` false, the fault-injection hook, it does not arrive) and polls the arrival count with
-// relaxed loads, sleeping 32 to 256 ns between polls, until it reaches `target`; one fence after the
-// last poll then acquires the other blocks' writes (a relaxed read followed by a fence is an acquire
-// in the PTX memory model).  Returns false in every thread of the block if the wait gave up: its own
-// limit was reached (the status word is set), or another block had set the status.
+// after it.  After the block's __syncthreads, thread 0 arrives with a release reduction on the
+// arrival counter (it orders the block's earlier writes before the arrival; with `arrive` false, the
+// fault-injection hook, it does not arrive) and polls the count with relaxed loads, spinning for 256
+// polls and then sleeping 64 ns between polls, until it reaches `target`; an acquire fence after the
+// last poll then orders the other blocks' writes before the block's later reads (a relaxed read
+// followed by a fence is an acquire in the PTX memory model).  Returns false in every thread of the
+// block if the wait gave up: its own limit was reached (the status word is set), or another block had
+// set the status.
 __device__ __forceinline__ bool grid_barrier(const PersistCtl &c, unsigned target, bool arrive)
 {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        __threadfence();
-        if (arrive) atomicAdd(c.arrive, 1u);
+        if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(c.arrive) : "memory");
         const uint64_t t0 = global_ns();
-        unsigned nap = 32;
         for (uint32_t it = 0;; ++it) {
             if (ld_relaxed_gpu(c.arrive) >= target) break;
             if (*(volatile const int32_t *)c.status != 0) {
@@ -755,10 +755,9 @@ __device__ __forceinline__ bool grid_barrier(const PersistCtl &c, unsigned targe
                 ok = 0;
                 break;
             }
-            __nanosleep(nap);
-            nap = nap < 256 ? 2 * nap : 256;
+            if (it > 256) __nanosleep(64);
         }
-        __threadfence();
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         s_ok = ok;
     }
     __syncthreads();
