@@ -98,21 +98,39 @@ def recorded_traffic(kernel: str, workload: str, prec: str, field: str = "bytes_
     return None
 
 
-# FP64 FMA peak of GB300 from its unit counts and clock: 152 SMs x 2 DFMA per cycle x 2 flops x
-# 2.07 GHz (the rate ncu reports as sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+def fp64_peak_tflops(sm_count: int | None = None, sm_mhz: float | None = None) -> float:
+    """FP64 FMA peak derived from the unit counts and clock: SMs x 2 DFMA per cycle x 2 flops x clock
+    (GB300: 152 SMs, 2.07 GHz: 1.26 TFLOP/s; the rate ncu reports as
+    sm__sass_thread_inst_executed_op_dfma_pred_on.sum.peak_sustained).  The SM count is read from the
+    device where there is one, the clock is the sampled maximum SM clock."""
+    return (sm_count or 152) * 2 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
-def fp64_alu_roofline(workload: str, facet_ms: float):
+FP64_PEAK_TFLOPS = fp64_peak_tflops()
+
+
+def fp64_alu_roofline(workload: str, facet_ms: float, facets: int | None = None, sm_count: int | None = None,
+                      sm_mhz: float | None = None):
     """The FP64 facet pass against the FP64 pipe: FP64 flops of one launch (dadd + dmul + 2 dfma,
-    counted by ncu on the same kernel source) over the live launch time."""
+    counted by ncu on the same kernel source) over the live launch time.  Without a capture of this
+    workload, the per-facet count of the 1.82M-facet uniaxial-tension capture is scaled by the facets
+    (another loading state: the branch mix differs), and the line says so."""
     fl = recorded_traffic("facet_kernel", workload, "fp64", "fp64_flops_per_launch")
+    how = "counted on this workload"
+    if fl is None and facets:
+        ref = recorded_traffic("facet_kernel", "uniaxial_tension", "fp64", "fp64_flops_per_launch")
+        if ref is not None:
+            fl = ref / 1820724 * facets
+            how = "scaled by facets from the uniaxial_tension capture (%.0f flops per facet)" % (ref / 1820724)
     if fl is None or not facet_ms:
         return None
+    peak = fp64_peak_tflops(sm_count, sm_mhz)
     achieved = fl / (facet_ms * 1e-3) / 1e12
-    return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP64_PEAK_TFLOPS, "flop_per_launch": fl,
-            "peak_source": "derived: 152 SMs x 2 DFMA/cycle x 2 flop x 2.07 GHz"}
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "flop_per_launch": fl, "flops": how,
+            "peak_source": "derived: %d SMs (from the device) x 2 DFMA/cycle x 2 flop x %.2f GHz (sampled maximum SM "
+                           "clock); no measured FP64 peak exists for this pool" % (sm_count or 152,
+                                                                                    (sm_mhz or 2070.0) / 1e3)}
 
 
 class ClockSampler:
@@ -391,8 +409,8 @@ def run_leg(name, wl, spec, bc, prec, steps, warmup, preroll, stream, flush_buf,
         "roofline": hbm_roofline(ref["facet_pass"] * F, fb, facet_ms, peak, peak_src,
                                  recorded_traffic(kern, name, prec),
                                  "%.0f B per facet-update (facet pass of a stored-frame layout)" % ref["facet_pass"]),
-        "gather_roofline": hbm_roofline(gb, gb, gather_ms, peak, peak_src, None, "design bytes (no stored-layout "
-                                                                                 "figure for the pass alone)"),
+        "gather_roofline": hbm_roofline(gb, gb, gather_ms, peak, peak_src, recorded_traffic("gather_kernel", name, prec),
+                                        "design bytes (no stored-layout figure for the pass alone)"),
         "step_roofline": step_roofline(ref["step"] * F, fb + gb, ms_step, peak, peak_src),
         "energy_err_pct": float(energy[3]),
         "sizes": {"particles": N, "tets": T, "facets": F},
@@ -425,7 +443,7 @@ def run_ours(args, rank, world, local):
                     peak_src, world, args.launch)
     fp64 = run_leg(args.workload, wl, spec, bc, "fp64", max(3, args.steps // 4), args.warmup, preroll, stream, flush,
                    peak, peak_src, world, args.launch)
-    fp64["alu_roofline"] = fp64_alu_roofline(args.workload, fp64["kernel_ms"]["facet"])
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
     extra = {}
     if not args.no_extra and args.workload != "uniaxial_tension":
         # the 1.82M-facet uniaxial-tension cube beside the headline
@@ -443,6 +461,8 @@ def run_ours(args, rank, world, local):
     if sampler:
         sampler.__exit__()
     clocks = sampler.summary() if sampler else None
+    fp64["alu_roofline"] = fp64_alu_roofline(args.workload, fp64["kernel_ms"]["facet"], F, sms,
+                                             (clocks or {}).get("sm_max_mhz"))
     # end to end through the C ABI with host buffers: create (H2D of the geometry), K steps each with an
     # energy/reaction read-back (D2H), final state read-back, destroy.
     barrier(world)

@@ -164,3 +164,31 @@ def test_elastic_vibration_persistent_fp64_conserves_energy():
     assert nrel(eb[:3], ea[:3]) <= 1e-10 and eb[3] < 1.0
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_persistent_with_per_facet_parameters(loaded, prec):
+    """The persistent kernel's per-facet parameter instantiation (E0, alpha, sigma_t per facet)."""
+    spec, bc, dt = loaded
+    rng = np.random.default_rng(7)
+    F = spec.n_facets
+    E0 = MAT["E0"] * rng.uniform(0.8, 1.2, F)
+    alpha = MAT["alpha"] * rng.uniform(0.8, 1.2, F)
+    sig = MAT["sigma_t"] * rng.uniform(0.7, 1.1, F)
+    a = ldpm.Model(spec, MAT, precision=prec, dt=dt, bc=bc)
+    b = ldpm.Model(spec, MAT, precision=prec, dt=dt, bc=bc)
+    ldpm.ldpm_set_launch_mode(b.h, ldpm.LDPM_LAUNCH_PERSISTENT)
+    for m in (a, b):
+        m.set_facet_params(E0, alpha, sig)
+        m.step(60)
+    assert_modes_agree(a.get_state(), b.get_state(), prec, "per-facet parameters")
+    if prec == "fp64":
+        o = oracle.Oracle(spec, MAT, dt, bc)
+        o.set_facet_params(E0, alpha, sig)
+        o.step(60)
+        qg, vg, hg, _ = b.get_state()
+        qo, vo, ho, _ = o.get_state()
+        for what, g, r in (("q", qg, qo), ("v", vg, vo), ("hist", hg, ho)):
+            assert_elementwise(g, r, 1e-9, what)
+    a.close()
+    b.close()
