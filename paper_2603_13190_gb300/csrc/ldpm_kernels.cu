@@ -692,7 +692,7 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
 }
 
 template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 21 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 20 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
     const int lane = threadIdx.x & 31;
     const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
@@ -1202,8 +1202,8 @@ template <class R, int LPP>
 cudaError_t launch_gather_lpp(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
 {
     const int64_t warps = ((int64_t)m.N + (32 / LPP) - 1) / (32 / LPP);
-    // blocks of 2 warps, 21 per SM at 48 registers: the particle sets of the benchmark specimens fit in
-    // one wave (blocks of 8 warps, 5 per SM, left a second one)
+    // blocks of 2 warps, up to 20 per SM at 48 registers (measured on GB300 against 8-warp blocks at 5 per
+    // SM and 2-warp blocks at 21 per SM, where the compiler keeps 40 registers and spills)
     const unsigned blocks = (unsigned)((warps * 32 + 63) / 64);
     switch (mode) {
     case GATHER_ASSEMBLE:
