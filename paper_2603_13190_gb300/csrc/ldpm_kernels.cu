@@ -471,8 +471,10 @@ __device__ __forceinline__ void facet_tile(const DeviceModel &m, const void *__r
     __syncwarp();  // the warp's shared rows may be reused for another tile
 }
 
+// Mixed mode: capped at 80 registers (12 blocks of 2 warps per SM); without the cap the multi-specimen
+// instantiation took 93 registers and ran 8 % slower on the 97.7M-facet batch (GB300, side by side).
 template <class R, int MODE, int WPB, bool PF, bool S1>
-__global__ void __launch_bounds__(32 * WPB)
+__global__ void __launch_bounds__(32 * WPB, sizeof(R) == 4 ? 12 : 1)
     facet_warp_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc)
 {
     constexpr int TETS = kTileTets;
