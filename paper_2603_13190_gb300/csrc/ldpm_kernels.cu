@@ -338,22 +338,20 @@ __device__ __forceinline__ void vertex_sum(const DeviceModel &m, int64_t tet0, i
     *reinterpret_cast<V2 *>(tvc + (tet0 + j) * 24 + 6 * v + 2 * q) = V2{s0, s1};
 }
 
-// PF: the facet's own E0, alpha, sigma_t (m.pf) replace the material's in the law.
-template <class R, int MODE, int TETS, bool PF>
-__global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const void *__restrict__ vsrc)
+// One tile of TETS tetrahedra run by a block of 12 TETS threads (one facet each): phases A-C above.
+// PF: the facet's own E0, alpha, sigma_t (m.pf) replace the material's in the law.  PERSIST: called
+// from the persistent step kernel (live data through ld_live; the block's shared rows are reused for
+// the next tile after the closing barrier).
+template <class R, int MODE, int TETS, bool PF, bool PERSIST>
+__device__ __forceinline__ void facet_block_tile(const DeviceModel &m, const void *__restrict__ vsrc, int64_t tet0,
+                                                 R (*sv)[Stride<R>::row], R (*scon)[Stride<R>::con], R *seV,
+                                                 int *sok)
 {
     using T4 = R4<R>;
     constexpr int E = 16 / (int)sizeof(R);  // elements per 16-byte shared-memory vector
-    __shared__ alignas(16) R sv[TETS * 4][Stride<R>::row];
-    __shared__ alignas(16) R scon[12 * TETS][Stride<R>::con];
-    __shared__ R seV[TETS];
-    __shared__ int sok[TETS];
     const T4 *__restrict__ geo = static_cast<const T4 *>(m.geo);
     const T4 *__restrict__ hist = static_cast<const T4 *>(m.hist);
-
     const int tid = threadIdx.x;
-    const int64_t tet0 = (int64_t)blockIdx.x * TETS;
-    if (MODE == FACET_STEP && blockIdx.x == 0 && tid == 0) *m.step += 1;
 
     // ---- prefetch this thread's facet data
     const int j = tid / 12;
@@ -363,12 +361,12 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
     T4 g{}, h{}, pp{};
     if (valid) {
         g = geo[f];
-        if (MODE != FACET_ELASTIC) h = hist[f];
+        if (MODE != FACET_ELASTIC) h = ld_live<PERSIST>(hist + f);
         if (PF) pp = static_cast<const T4 *>(m.pf)[f];
     }
 
     // ---- phase A: vertex records -> shared memory, e_V per tetrahedron
-    if (tid < 4 * TETS) stage_vertex<R, MODE>(m, vsrc, tet0, tid, sv, seV, sok);
+    if (tid < 4 * TETS) stage_vertex<R, MODE, PERSIST>(m, vsrc, tet0, tid, sv, seV, sok);
     __syncthreads();
 
     // ---- phase B: one facet
@@ -381,6 +379,19 @@ __global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const v
 
     // ---- phase C
     if (live && MODE != FACET_METRIC) vertex_sum<R>(m, tet0, j, slot, scon);
+    if (PERSIST) __syncthreads();
+}
+
+template <class R, int MODE, int TETS, bool PF>
+__global__ void __launch_bounds__(12 * TETS) facet_kernel(DeviceModel m, const void *__restrict__ vsrc)
+{
+    __shared__ alignas(16) R sv[TETS * 4][Stride<R>::row];
+    __shared__ alignas(16) R scon[12 * TETS][Stride<R>::con];
+    __shared__ R seV[TETS];
+    __shared__ int sok[TETS];
+    const int64_t tet0 = (int64_t)blockIdx.x * TETS;
+    if (MODE == FACET_STEP && blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
+    facet_block_tile<R, MODE, TETS, PF, false>(m, vsrc, tet0, sv, scon, seV, sok);
 }
 
 // Warp-tile variant of facet_kernel: every warp owns a tile of 8 tetrahedra and runs phases A-C on it
@@ -797,16 +808,54 @@ __global__ void __launch_bounds__(32 * WPB)
     }
 }
 
+// FP64 variant: the facet phase takes 8-tetrahedron tiles per block of 96 threads, one facet per thread
+// (facet_block_tile, as facet_kernel does), which gives the FP64 pipe 4x the warps of warp tiles with
+// three facets per lane.  The particle phase is the warp-level one of the kernel above.
+template <class R, bool PF>
+__global__ void __launch_bounds__(12 * kTileTets)
+    step_persistent_block_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc, int64_t nsteps,
+                                 PersistCtl ctl)
+{
+    constexpr int TETS = kTileTets;
+    constexpr int WPB = 12 * TETS / 32;
+    __shared__ alignas(16) R sv[TETS * 4][Stride<R>::row];
+    __shared__ alignas(16) R scon[12 * TETS][Stride<R>::con];
+    __shared__ R seV[TETS];
+    __shared__ int sok[TETS];
+    __shared__ int s_stop;
+    if (threadIdx.x == 0) s_stop = *(volatile const int32_t *)ctl.status;
+    __syncthreads();
+    if (s_stop != 0) return;  // an earlier launch gave up: no work (the whole block)
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t gw = (int64_t)blockIdx.x * WPB + w, nw = (int64_t)gridDim.x * WPB;
+    const int64_t tiles = m.T / TETS;
+    const int64_t groups = ((int64_t)m.N + 3) / 4;
+    unsigned target = 0;
+    for (int64_t n = 0; n < nsteps; ++n) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
+        for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x)
+            facet_block_tile<R, FACET_STEP, TETS, PF, true>(m, vsrc, t * TETS, sv, scon, seV, sok);
+        target += gridDim.x;
+        if (!grid_barrier(ctl, target, !(n == 0 && (int)blockIdx.x == ctl.skip_block))) return;
+        for (int64_t g = gw; g < groups; g += nw) gather_group<R, GATHER_STEP_MID, 8, true>(m, 4 * g + lane / 8, lane, nullptr);
+        target += gridDim.x;
+        if (!grid_barrier(ctl, target, true)) return;
+    }
+}
+
 template <class R, bool PF, bool S1>
 constexpr int persist_wpb()
 {
-    return sizeof(R) == 4 ? 4 : 2;  // static shared memory stays below 48 KB per block
+    return sizeof(R) == 4 ? 4 : 12 * kTileTets / 32;  // static shared memory stays below 48 KB per block
 }
 
 template <class R, bool PF, bool S1>
 const void *persist_fn()
 {
-    return reinterpret_cast<const void *>(&step_persistent_kernel<R, PF, S1, persist_wpb<R, PF, S1>()>);
+    if constexpr (sizeof(R) == 4)
+        return reinterpret_cast<const void *>(&step_persistent_kernel<R, PF, S1, persist_wpb<R, PF, S1>()>);
+    else
+        return reinterpret_cast<const void *>(&step_persistent_block_kernel<R, PF>);
 }
 
 // First half kick and drift of a stepping call: v_{n+1/2} = v_n + dt/2 a_n, q_{n+1} = q_n + dt v_{n+1/2}.
@@ -1132,7 +1181,7 @@ cudaError_t launch_persistent_r(const DeviceModel &m, int64_t nsteps, const Pers
 {
     const void *fn = (sizeof(R) == 4 && m.n_spec == 1) ? (m.pf ? persist_fn<R, true, true>() : persist_fn<R, false, true>())
                                                         : (m.pf ? persist_fn<R, true, false>() : persist_fn<R, false, false>());
-    const int threads = 32 * (sizeof(R) == 4 ? 4 : 2);
+    const int threads = 32 * persist_wpb<R, false, false>();
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1141,9 +1190,12 @@ cudaError_t launch_persistent_r(const DeviceModel &m, int64_t nsteps, const Pers
     if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
     // as many blocks as the device holds at once, but no more than the work needs: every block takes
     // part in every barrier, so idle blocks on a small specimen would only slow the barriers down
+    // (a tile takes a warp in the FP32 kernel and a block in the FP64 one; 4 particles take a warp)
     const int wpb = threads / 32;
-    const int64_t units = std::max<int64_t>(m.T / kTileTets, ((int64_t)m.N + 3) / 4);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, (units + wpb - 1) / wpb));
+    const int64_t tiles = m.T / kTileTets, groups = ((int64_t)m.N + 3) / 4;
+    const int64_t need = sizeof(R) == 4 ? (std::max(tiles, groups) + wpb - 1) / wpb
+                                        : std::max(tiles, (groups + wpb - 1) / wpb);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)per_sm * sms, need));
     if (grid_out) *grid_out = (int)grid;
     if (nsteps <= 0) return cudaSuccess;
     const void *vsrc = sizeof(R) == 4 ? static_cast<const void *>(m.pm32) : static_cast<const void *>(m.pstate);

@@ -192,3 +192,25 @@ def test_persistent_with_per_facet_parameters(loaded, prec):
             assert_elementwise(g, r, 1e-9, what)
     a.close()
     b.close()
+
+
+def test_adjoint_of_a_persistent_handle(loaded):
+    """ldpm_adjoint runs its own forward and reverse passes whatever the launch mode: a handle in the
+    persistent mode gives the gradient of one in launch pairs, and both end in the same state."""
+    spec, bc, dt = loaded
+    seed = np.zeros((spec.n_particles, 6))
+    seed[spec.face_nodes(2, 1), 2] = 1.0
+    out = []
+    for mode in (ldpm.LDPM_LAUNCH_PAIRS, ldpm.LDPM_LAUNCH_PERSISTENT):
+        m = ldpm.Model(spec, MAT, precision="fp64", dt=dt, bc=bc)
+        ldpm.ldpm_set_launch_mode(m.h, mode)
+        m.step(30)
+        J, gE, ga, gs = m.adjoint(40, seed, ckpt_every=16)
+        m.step(10)
+        out.append((J, gE, ga, gs, m.get_state()))
+        m.close()
+    (Ja, gEa, gaa, gsa, sa), (Jb, gEb, gab, gsb, sb) = out
+    assert abs(Ja - Jb) <= 1e-10 * abs(Ja)
+    for x, y in ((gEa, gEb), (gaa, gab), (gsa, gsb)):
+        assert nrel(y, x) <= 1e-9
+    assert_modes_agree(sa, sb, "fp64", "after the adjoint and 10 more steps")
