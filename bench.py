@@ -59,12 +59,16 @@ def facet_pass_bytes(F: int, T: int, N: int, r: int) -> float:
 
 
 # Algorithmic bytes of one particle-pass launch in the library's own layout.
-#   per tetrahedron  4 CSR slot ids (4 B) and the 4 shares read (24r)
-#   per particle     row pointer 4 B; q, v read and written 192 B; forces and energy sums read and
-#                    written 128 B; inverse masses, BC codes, specimen 64 B; mixed mode writes the
-#                    FP32 record 84 B
+#   per tetrahedron  the 4 shares read (24r)
+#   per particle     slot table 160 B (40 slot ids, -1 past the row's end; a longer row continues in
+#                    the CSR ids, not counted) and row pointer 4 B; q, v read and written 192 B; forces
+#                    and energy sums read and written 128 B; inverse masses, BC codes, specimen 64 B;
+#                    mixed mode writes the FP32 record 84 B
+SLOT_TABLE_BYTES = 160
+
+
 def gather_pass_bytes(T: int, N: int, r: int) -> float:
-    return T * 4 * (4 + 6 * r) + N * (4 + 192 + 128 + 64 + (84 if r == 4 else 0))
+    return T * 4 * 6 * r + N * (SLOT_TABLE_BYTES + 4 + 192 + 128 + 64 + (84 if r == 4 else 0))
 
 
 def kernel_src_hash() -> str:

@@ -239,7 +239,7 @@ void free_model(ldpm_ctx *h)
     void *ptrs[] = {h->dm.pstate, h->dm.pdyn, h->dm.pconst, h->dm.pm32, h->dm.bc_vel, h->dm.bc_vm, h->dm.f_ext,
                     h->dm.tet,
                     h->dm.geo,
-                    h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.tile_spec, h->dm.law, h->dm.spec,
+                    h->dm.hist, h->dm.fout, h->dm.tvc, h->dm.ent, h->dm.row, h->dm.stab, h->dm.tile_spec, h->dm.law, h->dm.spec,
                     h->dm.step, h->dm.flag, h->d_partial, h->d_out16, h->dm.pf, h->d_umap, h->d_scratch, h->d_ticket,
                     h->d_pmap, h->pctl.arrive, h->pctl.status};
     for (void *p : ptrs)
@@ -960,6 +960,7 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
         (rc = dalloc(&dm.pconst, 8 * (size_t)N)) || (rc = dalloc(&dm.bc_vel, 6 * (size_t)N)) ||
         (rc = dalloc(&dm.bc_vm, 6 * (size_t)N)) ||
         (rc = dalloc(&dm.tet, (size_t)T)) || (rc = dalloc(&dm.row, (size_t)N + 1)) ||
+        (rc = dalloc(&dm.stab, (size_t)kSlotTab * N)) ||
         (rc = dalloc(&dm.tile_spec, (size_t)T / kTile)) || (rc = dalloc(&dm.spec, (size_t)n)) ||
         (rc = dalloc(&dm.step, 1)) || (rc = dalloc(&dm.flag, 1)) || (rc = dalloc(&h->d_out16, 16)) ||
         (rc = dalloc(&h->d_partial, 16 * (size_t)((N + 255) / 256 + 1))) || (rc = dalloc(&h->d_umap, umap.size())) ||
@@ -992,6 +993,18 @@ int create_model(int n, const ldpm_geometry *geoms, const ldpm_material *mats, c
     CU(cudaMemcpy(dm.bc_vm, H.bc_vm.data(), H.bc_vm.size() * sizeof(double), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.tet, H.tet.data(), H.tet.size() * sizeof(int4), cudaMemcpyHostToDevice));
     CU(cudaMemcpy(dm.row, H.row.data(), H.row.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    {
+        // slot table: the first kSlotTab CSR entries of each particle, -1 after the row's end
+        std::vector<int32_t> stab((size_t)kSlotTab * N, -1);
+        parallel_min(N, [&](int64_t p0, int64_t p1) -> int64_t {
+            for (int64_t p = p0; p < p1; ++p) {
+                const int64_t r0 = H.row[p], n = std::min<int64_t>(H.row[p + 1] - r0, kSlotTab);
+                for (int64_t j = 0; j < n; ++j) stab[(size_t)p * kSlotTab + j] = (int32_t)H.ent_id[r0 + j];
+            }
+            return 0;
+        });
+        CU(cudaMemcpy(dm.stab, stab.data(), stab.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     CU(cudaMemcpy(dm.tile_spec, H.tile_spec.data(), H.tile_spec.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CU(cudaMemset(dm.step, 0, sizeof(int64_t)));
     CU(cudaMemset(dm.flag, 0, sizeof(int32_t)));
@@ -1262,7 +1275,6 @@ struct DevArena {
 // Byte sizes of the evolving state: everything a step reads and writes.
 struct StateBytes {
     size_t ps, pd, pm, hist;
-    size_t total() const { return ps + pd + pm + hist + 256; }
 };
 
 StateBytes state_bytes(const ldpm_ctx *h)

@@ -374,6 +374,75 @@ __device__ __forceinline__ ff ff_from_double(double x)
 }
 __device__ __forceinline__ double ff_to_double(ff a) { return f2d_bits(a.hi) + f2d_bits(a.lo); }
 
+// The same arithmetic on two float-float values at once (components x and y), with the packed FP32
+// instructions of sm_100 and later (one instruction per pair).  a - b is fma(b, -1, a): the product is
+// exact, so the single rounding equals that of a subtraction, and each component is bitwise the
+// scalar operation's result.
+struct ff2 {
+    float2 hi, lo;
+};
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ ff2 two_sum2(float2 a, float2 b)
+{
+    const float2 s = __fadd2_rn(a, b);
+    const float2 bb = f2_sub(s, a);
+    return {s, __fadd2_rn(f2_sub(a, f2_sub(s, bb)), f2_sub(b, bb))};
+}
+__device__ __forceinline__ ff2 fast_two_sum2(float2 a, float2 b)
+{
+    const float2 s = __fadd2_rn(a, b);
+    return {s, f2_sub(b, f2_sub(s, a))};
+}
+// a += x, componentwise (x a pair of floats)
+__device__ __forceinline__ void ff2_acc(ff2 &a, float2 x)
+{
+    const ff2 t = two_sum2(a.hi, x);
+    a.hi = t.hi;
+    a.lo = __fadd2_rn(a.lo, t.lo);
+}
+__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b)
+{
+    const ff2 s = two_sum2(a.hi, b.hi);
+    return fast_two_sum2(s.hi, __fadd2_rn(s.lo, __fadd2_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ ff2 ff2_shfl_xor(ff2 a, int off)
+{
+    ff2 r;
+    r.hi.x = __shfl_xor_sync(0xffffffffu, a.hi.x, off);
+    r.hi.y = __shfl_xor_sync(0xffffffffu, a.hi.y, off);
+    r.lo.x = __shfl_xor_sync(0xffffffffu, a.lo.x, off);
+    r.lo.y = __shfl_xor_sync(0xffffffffu, a.lo.y, off);
+    return r;
+}
+__device__ __forceinline__ ff2 ff2_pack(ff x, ff y) { return {make_float2(x.hi, y.hi), make_float2(x.lo, y.lo)}; }
+
+// Sum of three float-float pairs (components 0-1, 2-3, 4-5) over each aligned group of 8 lanes by
+// halving exchanges on pairs (the three padded with a zero pair to four: 2 + 1 pair additions, then
+// one scalar).  Afterwards lane L (L = lane & 7) holds the group sum of component L for L < 6 and
+// zero for L = 6, 7.  The order of the additions is fixed.
+__device__ __forceinline__ ff pair_halving_sum6(const ff2 (&v)[3], int lane)
+{
+    const ff2 zero = {make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+    ff2 w0, w1;
+    {
+        const bool upper = (lane & 4) != 0;
+        const ff2 keep0 = upper ? v[2] : v[0], give0 = upper ? v[0] : v[2];
+        const ff2 keep1 = upper ? zero : v[1], give1 = upper ? v[1] : zero;
+        w0 = ff2_add(keep0, ff2_shfl_xor(give0, 4));
+        w1 = ff2_add(keep1, ff2_shfl_xor(give1, 4));
+    }
+    ff2 u;
+    {
+        const bool upper = (lane & 2) != 0;
+        const ff2 keep = upper ? w1 : w0, give = upper ? w0 : w1;
+        u = ff2_add(keep, ff2_shfl_xor(give, 2));
+    }
+    const bool upper = (lane & 1) != 0;
+    const ff keep = upper ? ff{u.hi.y, u.lo.y} : ff{u.hi.x, u.lo.x};
+    const ff give = upper ? ff{u.hi.x, u.lo.x} : ff{u.hi.y, u.lo.y};
+    return ff_add(keep, ff_shfl_xor(give, 1));
+}
+
 // Accumulator operations shared by the FP64 sums (double) and the mixed-mode sums (float-float).
 __device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
 __device__ __forceinline__ ff acc_add(ff a, ff b) { return ff_add(a, b); }

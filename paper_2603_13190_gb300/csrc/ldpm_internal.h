@@ -20,6 +20,9 @@
 //                       vertex (3), in a fixed order
 //   row    [N+1]   i32  CSR of (tetrahedron, vertex) slots per particle, ascending tetrahedron
 //   ent    [4T]    i32  slot id 4 * tet + vertex
+//   stab   [N][40] i32  the first kSlotTab entries of each particle's CSR row, -1 after its last
+//                       entry: the particle pass reads a particle's slot ids from its index alone
+//                       (the rest of a longer row is read through row/ent)
 // Facet slot s of a tetrahedron belongs to edge e = s / 2 with local vertices
 // (a, b) in ((0,1),(0,2),(0,3),(1,2),(1,3),(2,3)); "I" of the internal facet is vertex a.
 #pragma once
@@ -30,6 +33,7 @@
 namespace ldpm {
 
 constexpr int kMirror = 24;  // floats per particle in the FP32 mirror
+constexpr int kSlotTab = 40; // slot ids per particle in stab (a multiple of 8 lanes)
 
 struct alignas(32) double4a {
     double x, y, z, w;
@@ -90,6 +94,7 @@ struct DeviceModel {
     void *hist_out = nullptr;  // where a stepping facet pass writes the new history (null: hist, in place)
     void *pf = nullptr;             // per-facet E0, alpha, sigma_t (R4 [12T]) or null
     int32_t *row = nullptr;
+    int32_t *stab = nullptr;        // [N][kSlotTab] slot ids per particle (see the layout above)
     int32_t *tile_spec = nullptr;   // [T / tets_per_block] specimen of each tile, or null (all 0)
     void *law = nullptr;            // LawConst<R>[n_spec]
     LawConst<float> law1{};         // mixed mode, one specimen: lawc[0] again, read from the kernel parameters

@@ -503,17 +503,17 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(R) == 4 ? 12 : 1)
 // ------------------------------------------------------------------------------------------------
 // Particle pass.  A group of LPP lanes owns one particle: it sums the particle's (tetrahedron,
 // vertex) contributions in CSR order (Eq. (2a)-(2b)), reduces across the group by halving exchanges,
-// after which lanes 0, 1, 2, 4, 5, 6 of the group hold components 0..5 and update one DOF each.  With
-// LPP = 8 a warp updates 4 particles per instruction.
+// after which six lanes of the group hold components 0..5 and update one DOF each.  With LPP = 8 a
+// warp updates 4 particles per instruction.
 // The particle's own records (mass, constraint, q, v, f_n) do not depend on the contributions and are
 // loaded before the sum, so their latency overlaps the CSR gather.
 // FP64 mode: everything is FP64.  Mixed mode: the shares are FP32 (each the sum of a tetrahedron's 6
-// FP32 facet terms at one vertex); the particle sums of the shares are float-float (48 mantissa bits),
-// converted to FP64 once; the velocity and displacement updates are FP64 as in FP64 mode; the energy
-// increments (trapezoid products and their 6-DOF sums) are float-float, added into the FP64
-// accumulators.  The GB300 FP64 pipe issues one warp instruction per
-// ~64 cycles per sub-partition, so the compensated sums run on the FP32 pipe; FP32 <-> FP64
-// conversions are integer operations.
+// FP32 facet terms at one vertex); the particle sums of the shares are float-float (48 mantissa bits;
+// components paired in packed FP32 instructions), converted to FP64 once; the velocity and
+// displacement updates are FP64; the energy increments (trapezoid products with v_{n+1/2} and their
+// 6-DOF sums) are float-float, scaled by dt/2 and added into the FP64 accumulators with one FP64 FMA
+// each.  The GB300 FP64 pipe issues one warp instruction per ~64 cycles per sub-partition, so the
+// compensated sums run on the FP32 pipe; FP32 <-> FP64 conversions are integer operations.
 // ------------------------------------------------------------------------------------------------
 // One group of LPP lanes, particle p (all 32 lanes of the warp take part in its shuffles).
 template <class R, int MODE, int LPP, bool PERSIST>
@@ -521,14 +521,14 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
 {
     static_assert(LPP == 8 || LPP == 16 || LPP == 32, "lanes per particle");
     constexpr bool kMixed = sizeof(R) == 4;
-    using Acc = typename std::conditional<kMixed, ff, double>::type;
     const int32_t *__restrict__ ent = static_cast<const int32_t *>(m.ent);
     const R *tvc = static_cast<const R *>(m.tvc);
     const int sub = lane & (LPP - 1);
     const bool valid = p < m.N;
-    // lanes 0, 1, 2, 4, 5, 6 of the group own DOFs 0..5 (where halving_sum6 leaves their sums); the
-    // other lanes mirror DOF 0 and store nothing
-    const int slot6 = sub < 8 ? halving_slot6(sub) : -1;
+    // after the group's reduction, lanes 0..5 (mixed: pair_halving_sum6) or 0, 1, 2, 4, 5, 6 (FP64:
+    // halving_sum6) of the group hold the sums of DOFs 0..5; the other lanes mirror DOF 0 and store
+    // nothing
+    const int slot6 = sub >= 8 ? -1 : kMixed ? (sub < 6 ? sub : -1) : halving_slot6(sub);
     const bool act = valid && slot6 >= 0;
     const int d = slot6 >= 0 ? slot6 : 0;
     const int64_t pc_ = valid ? p : 0;
@@ -552,20 +552,31 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
         q0 = ps[3 + d];
         if (has_fext) fe = m.f_ext[6 * pc_ + d];
     }
-    // each entry is one (tetrahedron, vertex) slot: 6 values, force (3) and moment about the particle (3)
-    // kSlots entries per lane in flight
-    constexpr int kSlots = 2;
-    Acc a[6];
+    // Each CSR entry is one (tetrahedron, vertex) slot: 6 values, force (3) and moment about the
+    // particle (3).  Lane `sub` sums entries sub, sub + LPP, sub + 2 LPP, ... of the particle's row in
+    // that order: the first kSlotTab from the slot table (all of them in flight at once, addressed by
+    // the particle index alone), the rest of a longer row through row/ent.
+    constexpr int KT = (kSlotTab + LPP - 1) / LPP;  // table positions per lane
+    const int32_t *__restrict__ tab = m.stab + (int64_t)pc_ * kSlotTab;
+    auto slot_id = [&](int k) -> int {
+        const int j = sub + LPP * k;
+        return (valid && j < kSlotTab) ? __ldg(tab + j) : -1;
+    };
+    const int j_over = sub + LPP * ((kSlotTab - sub + LPP - 1) / LPP);  // this lane's first entry past the table
+    double fa_new;
+    ff fa_ff{};  // mixed: the same sum as a float-float
+    if constexpr (kMixed) {
+        // components (0, 1), (2, 3), (4, 5) as packed float-float pairs
+        ff2 a[3];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) a[k] = Acc{};
-    for (int r = r0 + sub; r < r1; r += kSlots * LPP) {
-        int id[kSlots];
+        for (int c = 0; c < 3; ++c) a[c] = ff2{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)};
+        {
+            int id[KT];
 #pragma unroll
-        for (int k = 0; k < kSlots; ++k) id[k] = (r + k * LPP < r1) ? ent[r + k * LPP] : -1;
-        if constexpr (kMixed) {
-            float2 w[kSlots][3];
+            for (int k = 0; k < KT; ++k) id[k] = slot_id(k);
+            float2 w[KT][3];
 #pragma unroll
-            for (int k = 0; k < kSlots; ++k)
+            for (int k = 0; k < KT; ++k)
                 if (id[k] >= 0) {
                     const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)id[k]);
                     w[k][0] = ld_live<PERSIST>(src);
@@ -573,18 +584,36 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
                     w[k][2] = ld_live<PERSIST>(src + 2);
                 }
 #pragma unroll
-            for (int k = 0; k < kSlots; ++k)
+            for (int k = 0; k < KT; ++k)
                 if (id[k] >= 0) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        ff_acc(a[2 * c], w[k][c].x);
-                        ff_acc(a[2 * c + 1], w[k][c].y);
-                    }
+                    for (int c = 0; c < 3; ++c) ff2_acc(a[c], w[k][c]);
                 }
-        } else {
-            double2 w[kSlots][3];
+        }
+        for (int j = j_over; j < r1 - r0; j += LPP) {  // rows longer than the table
+            const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)ent[r0 + j]);
 #pragma unroll
-            for (int k = 0; k < kSlots; ++k)
+            for (int c = 0; c < 3; ++c) ff2_acc(a[c], ld_live<PERSIST>(src + c));
+        }
+        // lanes beyond the first 8 of a group fold into them
+#pragma unroll
+        for (int off = LPP / 2; off >= 8; off >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[c] = ff2_add(a[c], ff2_shfl_xor(a[c], off));
+        if (MODE != GATHER_ASSEMBLE) fa_old = pd[d];  // f_n: needed only by the energy increments
+        fa_ff = ff_norm(pair_halving_sum6(a, lane));
+        fa_new = ff_to_double(fa_ff);
+    } else {
+        double a[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = 0.0;
+        {
+            int id[KT];
+#pragma unroll
+            for (int k = 0; k < KT; ++k) id[k] = slot_id(k);
+            double2 w[KT][3];
+#pragma unroll
+            for (int k = 0; k < KT; ++k)
                 if (id[k] >= 0) {
                     const double2 *src = reinterpret_cast<const double2 *>(tvc + 6 * (int64_t)id[k]);
                     w[k][0] = ld_live<PERSIST>(src);
@@ -592,7 +621,7 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
                     w[k][2] = ld_live<PERSIST>(src + 2);
                 }
 #pragma unroll
-            for (int k = 0; k < kSlots; ++k)
+            for (int k = 0; k < KT; ++k)
                 if (id[k] >= 0) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
@@ -601,20 +630,23 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
                     }
                 }
         }
-    }
-    // lanes beyond the first 8 of a group fold into them, then the halving sum leaves component
-    // halving_slot6(sub & 7) of the particle's total in a[0]
+        for (int j = j_over; j < r1 - r0; j += LPP) {  // rows longer than the table
+            const double2 *src = reinterpret_cast<const double2 *>(tvc + 6 * (int64_t)ent[r0 + j]);
 #pragma unroll
-    for (int off = LPP / 2; off >= 8; off >>= 1)
+            for (int c = 0; c < 3; ++c) {
+                const double2 w = ld_live<PERSIST>(src + c);
+                a[2 * c] += w.x;
+                a[2 * c + 1] += w.y;
+            }
+        }
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] = acc_add(a[k], acc_shfl_xor(a[k], off));
-    if (MODE != GATHER_ASSEMBLE) fa_old = pd[d];  // f_n: needed only by the energy increments
-    halving_sum6(a, lane);
-    double fa_new;
-    if constexpr (kMixed)
-        fa_new = ff_to_double(ff_norm(a[0]));
-    else
+        for (int off = LPP / 2; off >= 8; off >>= 1)
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], off);
+        if (MODE != GATHER_ASSEMBLE) fa_old = pd[d];
+        halving_sum6(a, lane);
         fa_new = a[0];
+    }
     if (MODE == GATHER_ASSEMBLE) {
         if (act) out6[6 * p + d] = fa_new;
         return;
@@ -636,8 +668,13 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
     }
     double v_next, dWi_acc, dWe_acc;
     if (mask == 0) {
-        const double dv = (has_fext ? fe + fa_new : fa_new) * (hdt * im);  // dt/2 a_{n+1}
-        v_next = (vh + dv) + dv;
+        const double fa = has_fext ? fe + fa_new : fa_new;
+        if constexpr (kMixed) {
+            v_next = fma(fa, dt * im, vh);  // v_{n+3/2} = v_{n+1/2} + dt a_{n+1}
+        } else {
+            const double dv = fa * (hdt * im);  // dt/2 a_{n+1}
+            v_next = (vh + dv) + dv;
+        }
     } else {
         v_next = mask == 1 ? 0.0 : v_bc;
     }
@@ -645,8 +682,10 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
     //   dW_int = -(f_n + f_{n+1}) dq / 2 on every DOF, dW_ext = g dq / 2 with g the sum of the
     //   external forces (2 f_ext on loaded DOFs, the supports' reactions on constrained ones)
     if constexpr (kMixed) {
-        const ff fsum = ff_add(ff_from_double(fa_old), ff_from_double(fa_new));
-        const ff hdq = ff_mul(ff_from_double(hdt), ff_from_double(vh));
+        // float-float products with v_{n+1/2}, summed over the six DOFs as one packed pair
+        // (internal, external); the common factor dt/2 is applied in FP64 when accumulating
+        const ff fsum = ff_add(ff_from_double(fa_old), fa_ff);
+        const ff vhf = ff_from_double(vh);
         ff g = {0.0f, 0.0f};
         if (mask == 0) {
             if (has_fext) {
@@ -656,17 +695,13 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
         } else {
             g = mask == 1 ? ff_neg(fsum) : ff_add(ff_from_double(g_bc), ff_neg(fsum));
         }
-        ff dWi = act ? ff_neg(ff_mul(fsum, hdq)) : ff{0.0f, 0.0f};
-        ff dWe = (need_we && act) ? ff_mul(g, hdq) : ff{0.0f, 0.0f};
-        // sum the six DOF contributions into lane 0 of the group (lanes 3, 7 hold zeros)
+        const ff zero = {0.0f, 0.0f};
+        ff2 e = ff2_pack(act ? ff_neg(ff_mul(fsum, vhf)) : zero, (need_we && act) ? ff_mul(g, vhf) : zero);
+        // the six DOF contributions into every lane of the group (lanes 6, 7 hold zeros)
 #pragma unroll
-        for (int off = 4; off > 0; off >>= 1) dWi = ff_add(dWi, ff_shfl_xor(dWi, off));
-        if (need_we) {
-#pragma unroll
-            for (int off = 4; off > 0; off >>= 1) dWe = ff_add(dWe, ff_shfl_xor(dWe, off));
-        }
-        dWi_acc = ff_to_double(dWi);
-        dWe_acc = need_we ? ff_to_double(dWe) : 0.0;
+        for (int off = 4; off > 0; off >>= 1) e = ff2_add(e, ff2_shfl_xor(e, off));
+        dWi_acc = f2d_bits(e.hi.x) + f2d_bits(e.lo.x);
+        dWe_acc = need_we ? f2d_bits(e.hi.y) + f2d_bits(e.lo.y) : 0.0;
     } else {
         double g_sum = 0.0;
         if (mask == 0) {
@@ -698,14 +733,19 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
         if (m.pm32) write_mirror(m.pm32 + kMirror * pc_, d, q, v_next);
         if (!finite_bits(v_next) || !finite_bits(q)) *(volatile int32_t *)m.flag = 1;
         if (sub == 0) {
-            pd[6] += dWi_acc;
-            if (need_we) pd[7] += dWe_acc;
+            if constexpr (kMixed) {
+                pd[6] = fma(hdt, dWi_acc, pd[6]);
+                if (need_we) pd[7] = fma(hdt, dWe_acc, pd[7]);
+            } else {
+                pd[6] += dWi_acc;
+                if (need_we) pd[7] += dWe_acc;
+            }
         }
     }
 }
 
 template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 20 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 16 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
     const int lane = threadIdx.x & 31;
     const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
@@ -1256,8 +1296,8 @@ template <class R, int LPP>
 cudaError_t launch_gather_lpp(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
 {
     const int64_t warps = ((int64_t)m.N + (32 / LPP) - 1) / (32 / LPP);
-    // blocks of 2 warps, up to 20 per SM at 48 registers (measured on GB300 against 8-warp blocks at 5 per
-    // SM and 2-warp blocks at 21 per SM, where the compiler keeps 40 registers and spills)
+    // blocks of 2 warps, up to 16 per SM at 60 registers (mixed mode; measured on GB300 against 12 and
+    // 20 per SM, where the compiler spills, and against 8-warp blocks)
     const unsigned blocks = (unsigned)((warps * 32 + 63) / 64);
     switch (mode) {
     case GATHER_ASSEMBLE:

@@ -18,7 +18,9 @@ def test_counters_follow_the_per_unit_formulas():
     # per facet 12R (geometry 4R, history 8R), per tetrahedron 16 B + 24R, per particle 84 / 120 B
     assert mixed["facet_pass_bytes"] == F * 48 + T * (16 + 96) + N * 84
     assert fp64["facet_pass_bytes"] == F * 96 + T * (16 + 192) + N * 120
-    assert mixed["particle_pass_bytes"] == T * 4 * (4 + 24) + N * (4 + 192 + 128 + 64 + 84)
+    # per tetrahedron 4 shares of 24R, per particle a 160 B slot table, row pointer 4 B, state and records
+    assert mixed["particle_pass_bytes"] == T * 4 * 24 + N * (160 + 4 + 192 + 128 + 64 + 84)
+    assert fp64["particle_pass_bytes"] == T * 4 * 48 + N * (160 + 4 + 192 + 128 + 64)
     for d in (mixed, fp64):
         assert d["step_bytes"] == d["facet_pass_bytes"] + d["particle_pass_bytes"]
         assert d["adjoint_step_bytes"] == 2 * d["step_bytes"] + d["reverse_facet_pass_bytes"] + \

@@ -207,3 +207,21 @@ def test_mixed_energy_sums_follow_the_fp64_path():
           % (rel_int.max(), rel_ext.max()))
     assert b[-1, 0] > 0 and b[-1, 1] > 0
     assert rel_int.max() <= 1e-6 and rel_ext.max() <= 1e-6
+
+
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_particles_beyond_the_slot_table(monkeypatch, lanes):
+    """The particle pass reads a particle's first 40 (tetrahedron, vertex) slot ids from a per-particle
+    table and continues a longer row through the CSR arrays.  On a cube with widely graded sizes
+    (particles with up to ~74 slots, five entries past the table per lane of 8) every lane count gives
+    the oracle's node forces, velocities and displacements."""
+    spec = specimen.shuffled(specimen.make_cube_specimen(12.0, 0.8, 5.0, 800, seed=11), seed=2)
+    cnt = np.bincount(np.asarray(spec.tets).ravel(), minlength=spec.n_particles)
+    assert cnt.max() > 64 and np.sum(cnt > 40) >= 5
+    bc, dt, o = loaded_state(spec, steps=150)
+    monkeypatch.setenv("LDPM_GATHER_LANES", str(lanes))
+    r = compare_one_step(spec, bc, dt, o, "fp64")
+    for k in ("f0", "f", "v", "q"):
+        assert_elementwise(*r[k], 1e-10, k)
+    rm = compare_one_step(spec, bc, dt, o, "mixed")
+    assert nrel(*rm["f0"]) <= 2e-5 and nrel(*rm["f"]) <= 2e-5, (nrel(*rm["f0"]), nrel(*rm["f"]))
