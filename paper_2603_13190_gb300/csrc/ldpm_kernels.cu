@@ -574,21 +574,27 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
             int id[KT];
 #pragma unroll
             for (int k = 0; k < KT; ++k) id[k] = slot_id(k);
-            float2 w[KT][3];
+            // the shares in batches of KB entries in flight (all ids are loaded above): 48 registers,
+            // 20 blocks of 64 threads per SM
+            constexpr int KB = 2;
 #pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if (id[k] >= 0) {
-                    const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)id[k]);
-                    w[k][0] = ld_live<PERSIST>(src);
-                    w[k][1] = ld_live<PERSIST>(src + 1);
-                    w[k][2] = ld_live<PERSIST>(src + 2);
-                }
+            for (int k0 = 0; k0 < KT; k0 += KB) {
+                float2 w[KB][3];
 #pragma unroll
-            for (int k = 0; k < KT; ++k)
-                if (id[k] >= 0) {
+                for (int k = k0; k < k0 + KB && k < KT; ++k)
+                    if (id[k] >= 0) {
+                        const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)id[k]);
+                        w[k - k0][0] = ld_live<PERSIST>(src);
+                        w[k - k0][1] = ld_live<PERSIST>(src + 1);
+                        w[k - k0][2] = ld_live<PERSIST>(src + 2);
+                    }
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) ff2_acc(a[c], w[k][c]);
-                }
+                for (int k = k0; k < k0 + KB && k < KT; ++k)
+                    if (id[k] >= 0) {
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) ff2_acc(a[c], w[k - k0][c]);
+                    }
+            }
         }
         for (int j = j_over; j < r1 - r0; j += LPP) {  // rows longer than the table
             const float2 *src = reinterpret_cast<const float2 *>(tvc + 6 * (int64_t)ent[r0 + j]);
@@ -745,7 +751,7 @@ __device__ __forceinline__ void gather_group(const DeviceModel &m, int64_t p, in
 }
 
 template <class R, int MODE, int LPP>
-__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 16 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
+__global__ void __launch_bounds__(64, sizeof(R) == 4 ? 20 : 1) gather_kernel(DeviceModel m, double *__restrict__ out6)
 {
     const int lane = threadIdx.x & 31;
     const int64_t p = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * (32 / LPP) + lane / LPP;
@@ -1296,8 +1302,8 @@ template <class R, int LPP>
 cudaError_t launch_gather_lpp(const DeviceModel &m, int mode, double *out6, cudaStream_t s)
 {
     const int64_t warps = ((int64_t)m.N + (32 / LPP) - 1) / (32 / LPP);
-    // blocks of 2 warps, up to 16 per SM at 60 registers (mixed mode; measured on GB300 against 12 and
-    // 20 per SM, where the compiler spills, and against 8-warp blocks)
+    // blocks of 2 warps, up to 20 per SM at 48 registers (mixed mode; measured on GB300 against 12, 16
+    // and 18 per SM with more shares in flight, and against 8-warp blocks)
     const unsigned blocks = (unsigned)((warps * 32 + 63) / 64);
     switch (mode) {
     case GATHER_ASSEMBLE:
