@@ -116,22 +116,17 @@ FP64_PEAK_TFLOPS = fp64_peak_tflops()
 def fp64_alu_roofline(workload: str, facet_ms: float, facets: int | None = None, sm_count: int | None = None,
                       sm_mhz: float | None = None):
     """The FP64 facet pass against the FP64 pipe: FP64 flops of one launch (dadd + dmul + 2 dfma,
-    counted by ncu on the same kernel source) over the live launch time.  Without a capture of this
-    workload, the per-facet count of the 1.82M-facet uniaxial-tension capture is scaled by the facets
-    (another loading state: the branch mix differs), and the line says so."""
+    counted by ncu on the same kernel source and workload) over the live launch time.  The count
+    depends on the loading state (which branch of the law each facet takes: 503 flops per facet on
+    the tension cube, 297.5 on the confined-compression headline), so a workload without its own
+    capture reports null rather than another workload's count scaled."""
     fl = recorded_traffic("facet_kernel", workload, "fp64", "fp64_flops_per_launch")
-    how = "counted on this workload"
-    if fl is None and facets:
-        ref = recorded_traffic("facet_kernel", "uniaxial_tension", "fp64", "fp64_flops_per_launch")
-        if ref is not None:
-            fl = ref / 1820724 * facets
-            how = "scaled by facets from the uniaxial_tension capture (%.0f flops per facet)" % (ref / 1820724)
     if fl is None or not facet_ms:
         return None
     peak = fp64_peak_tflops(sm_count, sm_mhz)
     achieved = fl / (facet_ms * 1e-3) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": achieved / peak, "flop_per_launch": fl, "flops": how,
+            "frac": achieved / peak, "flop_per_launch": fl, "flops": "counted on this workload",
             "peak_source": "derived: %d SMs (from the device) x 2 DFMA/cycle x 2 flop x %.2f GHz (sampled maximum SM "
                            "clock); no measured FP64 peak exists for this pool" % (sm_count or 152,
                                                                                     (sm_mhz or 2070.0) / 1e3)}

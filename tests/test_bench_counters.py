@@ -85,12 +85,14 @@ def test_reference_arm_uses_the_workload_time_step_and_window():
         assert w.dt > 0, name
 
 
-def test_fp64_alu_roofline_scales_another_capture_by_facets(monkeypatch):
-    """Without a capture of the workload, the uniaxial-tension flops per facet times the facets, and the
-    line says so; the peak takes the device's SM count and the sampled clock."""
+def test_fp64_alu_roofline_needs_a_count_of_the_same_workload(monkeypatch):
+    """The FP64 flops of the facet pass depend on the loading state (the law's branch mix), so a
+    workload without its own capture has no ALU roofline; with one, the peak takes the device's SM
+    count and the sampled clock."""
     counts = {"uniaxial_tension": 1820724 * 500.0}
     monkeypatch.setattr(bench, "recorded_traffic", lambda k, w, p, f="bytes_per_launch": counts.get(w))
+    assert bench.fp64_alu_roofline("confined_compression", 5.0, facets=12535080, sm_count=148, sm_mhz=2000.0) is None
+    counts["confined_compression"] = 12535080 * 300.0
     r = bench.fp64_alu_roofline("confined_compression", 5.0, facets=12535080, sm_count=148, sm_mhz=2000.0)
-    assert abs(r["flop_per_launch"] - 12535080 * 500.0) < 1e-3 and "scaled by facets" in r["flops"]
+    assert abs(r["flop_per_launch"] - 12535080 * 300.0) < 1e-3 and r["flops"] == "counted on this workload"
     assert abs(r["peak"] - 148 * 2 * 2 * 2.0e9 / 1e12) < 1e-12 and "148 SMs" in r["peak_source"]
-    assert bench.fp64_alu_roofline("confined_compression", 5.0) is None
