@@ -72,9 +72,11 @@ def gather_pass_bytes(T: int, N: int, r: int) -> float:
 
 
 def kernel_src_hash() -> str:
+    """Hash of the kernel sources and of the build script (its compiler flags shape the kernels)."""
     h = hashlib.sha256()
     for f in ("ldpm_kernels.cu", "ldpm_adjoint.cu", "ldpm_device.cuh", "ldpm_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "csrc", f), "rb").read())
+    h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "build.py"), "rb").read())
     return h.hexdigest()[:16]
 
 

@@ -43,8 +43,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         extra = []
         if src in ("ldpm_kernels.cu", "ldpm_adjoint.cu"):
-            # approximate FP32 division and square root: only the mixed-mode arithmetic is FP32
-            extra = ["-prec-div=false", "-prec-sqrt=false"]
+            # approximate FP32 division and square root, FP32 subnormals flushed to zero: only the
+            # mixed-mode arithmetic is FP32, and its law enters the fracture branch only for strains
+            # >= 1e-15 (subnormal FP32 values arise only in vanishing jumps ahead of a loading wave).
+            # Without the flush every FP32 square root, reciprocal and exponential carries its
+            # subnormal range handling: 7 % of the facet pass on the 1.82M-facet cube (GB300).
+            extra = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
         cmd = [nvcc()] + common + extra + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
