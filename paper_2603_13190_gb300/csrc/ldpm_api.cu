@@ -226,6 +226,8 @@ struct ldpm_ctx {
     int launch_mode = LDPM_LAUNCH_PAIRS;
     PersistCtl pctl;          // device words arrive / status of the persistent kernel's grid barriers
     int persist_grid = 0;     // its grid (co-resident blocks), 0 until the mode is first chosen
+    BatchLaw batch_law{};     // mixed-mode batches of 2..kParamSpecimens specimens: law constants for the
+                              // kernel parameters of the FP32 facet pass (n = 0 otherwise)
     size_t rsize() const { return prec == LDPM_MIXED ? sizeof(float) : sizeof(double); }
     size_t r4size() const { return 4 * rsize(); }
 };
@@ -589,12 +591,23 @@ int update_law(ldpm_ctx *h)
         std::vector<LawConst<float>> law(h->sp.size());
         for (size_t s = 0; s < h->sp.size(); ++s) law_const<float>(h->sp[s].mat, h->sp[s].dt, law[s]);
         CU(cudaMemcpy(h->dm.law, law.data(), law.size() * sizeof(law[0]), cudaMemcpyHostToDevice));
-        if (std::memcmp(&h->dm.law1, &law[0], sizeof(law[0])) != 0) {
-            // the copy travels in the kernel parameters: captured launches hold the old one
+        BatchLaw bl{};
+        const int n = (int)h->sp.size();
+        if (n > 1 && n <= kParamSpecimens) {
+            bl.n = n;
+            for (int s = 0; s < n; ++s) {
+                bl.t0[s] = h->sp[s].t0;
+                bl.law[s] = law[s];
+            }
+            bl.t0[n] = h->dm.T;
+        }
+        if (std::memcmp(&h->dm.law1, &law[0], sizeof(law[0])) != 0 || std::memcmp(&h->batch_law, &bl, sizeof(bl)) != 0) {
+            // the copies travel in the kernel parameters: captured launches hold the old ones
             CU(cudaStreamSynchronize(h->stream));
             for (auto &kv : h->graphs) cudaGraphExecDestroy(kv.second);
             h->graphs.clear();
             h->dm.law1 = law[0];
+            h->batch_law = bl;
         }
     } else {
         std::vector<LawConst<double>> law(h->sp.size());
@@ -612,8 +625,9 @@ int update_law(ldpm_ctx *h)
 
 int launch_facet_any(ldpm_ctx *h, int mode, const void *pst)
 {
-    cudaError_t e = h->prec == LDPM_MIXED ? launch_facet<float>(h->dm, mode, pst, h->stream)
-                                          : launch_facet<double>(h->dm, mode, pst, h->stream);
+    cudaError_t e = h->prec == LDPM_MIXED
+                        ? launch_facet<float>(h->dm, mode, pst, h->stream, h->batch_law.n ? &h->batch_law : nullptr)
+                        : launch_facet<double>(h->dm, mode, pst, h->stream);
     if (e != cudaSuccess) return fail(LDPM_E_CUDA, "facet pass launch: %s", cudaGetErrorString(e));
     return LDPM_OK;
 }

@@ -67,6 +67,16 @@ struct LawConst {
     int32_t elastic;
 };
 
+// Law constants of a batch of up to kParamSpecimens specimens for the kernel parameters of the FP32
+// facet pass (the copy in `law` serves larger batches).  A facet-pass block of 16 tetrahedra never
+// straddles two specimens (each is padded to 32), so a block finds its specimen from t0.
+constexpr int kParamSpecimens = 64;
+struct BatchLaw {
+    int32_t n = 0;                     // specimens; 0: not in use
+    int32_t t0[kParamSpecimens + 1];   // first internal tetrahedron of each specimen, t0[n] = T
+    LawConst<float> law[kParamSpecimens];
+};
+
 // Per-specimen time integration constants (FP64).
 struct SpecDyn {
     double dt, ramp_time;
@@ -160,7 +170,8 @@ cudaError_t launch_persistent(const DeviceModel &m, int64_t nsteps, const Persis
 // `src_override` replaces the particle records the facet pass reads (FP64 mode: pstate layout;
 // mixed mode: pm32 layout); null = the model's own.
 template <class R>
-cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s);
+cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s,
+                         const BatchLaw *bl = nullptr);
 // q += dq on free DOFs of the drifted state (dq [N][6] internal order, device), mirror updated.
 cudaError_t launch_perturb(const DeviceModel &m, const double *dq, cudaStream_t s);
 // Rebuild the FP32 mirror from pstate (after create, set_state, checkpoint load).  No-op in FP64.

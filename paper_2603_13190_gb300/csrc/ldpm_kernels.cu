@@ -196,7 +196,8 @@ __device__ __forceinline__ void stage_vertex(const DeviceModel &m, const void *_
 template <class R, int MODE, bool PF, bool S1 = false>
 __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, int j, int slot, int64_t f, bool live,
                                           const R4<R> &g, const R4<R> &h, const R4<R> &pp,
-                                          const R (*sv)[Stride<R>::row], const R *seV, R cs[12])
+                                          const R (*sv)[Stride<R>::row], const R *seV, R cs[12],
+                                          const LawConst<R> *lbatch = nullptr)
 {
     using T4 = R4<R>;
     constexpr int E = 16 / (int)sizeof(R);
@@ -227,7 +228,9 @@ __device__ __forceinline__ void facet_one(const DeviceModel &m, int64_t tet0, in
     const V3<R> cb = ca - d;
     R tN, tM, tL, emax;
     const LawConst<R> *lsrc;
-    if constexpr (S1 && sizeof(R) == 4) {
+    if (lbatch) {  // the batch kernel's parameters
+        lsrc = lbatch;
+    } else if constexpr (S1 && sizeof(R) == 4) {
         lsrc = reinterpret_cast<const LawConst<R> *>(&m.law1);
     } else {
         const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;  // specimens are padded to 32 tetrahedra
@@ -414,7 +417,8 @@ constexpr int kPlane = 6 * 4 * kTileTets + 2;
 // PERSIST: called from the persistent step kernel (live data through ld_live).
 template <class R, int MODE, bool PF, bool S1, bool PERSIST>
 __device__ __forceinline__ void facet_tile(const DeviceModel &m, const void *__restrict__ vsrc, int64_t tet0,
-                                           int lane, R (*sv)[Stride<R>::row], R *spl, R *seV, int *sok)
+                                           int lane, R (*sv)[Stride<R>::row], R *spl, R *seV, int *sok,
+                                           const LawConst<R> *lbatch = nullptr)
 {
     using T4 = R4<R>;
     using V2 = typename VecT<R>::v2;
@@ -443,7 +447,7 @@ __device__ __forceinline__ void facet_tile(const DeviceModel &m, const void *__r
         const bool live = tet0 + j < m.T && sok[j];
         const int slot = fi - 12 * j;
         R cs[12];
-        facet_one<R, MODE, PF, S1>(m, tet0, j, slot, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs);
+        facet_one<R, MODE, PF, S1>(m, tet0, j, slot, tet0 * 12 + fi, live, g[i], h[i], pp[i], sv, seV, cs, lbatch);
         if (MODE != FACET_METRIC) {
             // edge e = slot / 2 joins local vertices va < vb; it is the ka-th edge of va and the kb-th
             // of vb (ascending), so this facet is entry 2 ka + slot % 2 of va's order, 2 kb + slot % 2 of vb's
@@ -498,6 +502,40 @@ __global__ void __launch_bounds__(32 * WPB, sizeof(R) == 4 ? 12 : 1)
     if (MODE == FACET_STEP && blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
     if (tet0 >= m.T) return;  // whole warp (T is a multiple of the tile)
     facet_tile<R, MODE, PF, S1, false>(m, vsrc, tet0, lane, sv_[w], spl_[w], seV_[w], sok_[w]);
+}
+
+// The same for a batch of specimens, their law constants in the kernel parameters: a block of WPB
+// 8-tetrahedron tiles (16 tetrahedra) lies within one specimen, found from the block index alone by
+// a search over the specimens' first tetrahedra (all in the parameters), so the constants are read
+// at a block-uniform index.
+template <int MODE, int WPB, bool PF>
+__global__ void __launch_bounds__(32 * WPB, 12)
+    facet_warp_batch_kernel(const __grid_constant__ DeviceModel m, const void *__restrict__ vsrc,
+                            const __grid_constant__ BatchLaw bl)
+{
+    static_assert(WPB * kTileTets <= 32 && 32 % (WPB * kTileTets) == 0, "a block within one 32-tetrahedron unit");
+    constexpr int TETS = kTileTets;
+    __shared__ alignas(16) float sv_[WPB][TETS * 4][Stride<float>::row];
+    __shared__ alignas(16) float spl_[WPB][6 * kPlane];
+    __shared__ float seV_[WPB][TETS];
+    __shared__ int sok_[WPB][TETS];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t tet0 = ((int64_t)blockIdx.x * WPB + w) * TETS;
+    const int32_t tb = (int32_t)blockIdx.x * (WPB * TETS);
+    int lo = 0, hi = bl.n;  // bl.t0[lo] <= tb < bl.t0[hi]
+#pragma unroll
+    for (int it = 0; it < 7; ++it) {  // 2^7 > kParamSpecimens
+        const int mid = (lo + hi) >> 1;
+        if (hi - lo > 1) {
+            if (bl.t0[mid] <= tb)
+                lo = mid;
+            else
+                hi = mid;
+        }
+    }
+    if (MODE == FACET_STEP && blockIdx.x == 0 && threadIdx.x == 0) *m.step += 1;
+    if (tet0 >= m.T) return;  // whole warp (T is a multiple of the tile)
+    facet_tile<float, MODE, PF, false, false>(m, vsrc, tet0, lane, sv_[w], spl_[w], seV_[w], sok_[w], &bl.law[lo]);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1178,7 +1216,7 @@ __global__ void hist_from_user_kernel(DeviceModel m, const double *__restrict__ 
 }
 
 template <class R, int MODE, bool PF>
-cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t s)
+cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t s, const BatchLaw *bl)
 {
     const int tpb = m.tets_per_block;
     const unsigned blocks = (unsigned)((m.T + tpb - 1) / tpb);
@@ -1192,6 +1230,8 @@ cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t 
         const unsigned nb = (unsigned)((tiles + WPB - 1) / WPB);
         if (m.n_spec == 1)
             facet_warp_kernel<R, MODE, WPB, PF, true><<<nb, 32 * WPB, 0, s>>>(m, pst);
+        else if (bl && bl->n == m.n_spec)
+            facet_warp_batch_kernel<MODE, WPB, PF><<<nb, 32 * WPB, 0, s>>>(m, pst, *bl);
         else
             facet_warp_kernel<R, MODE, WPB, PF, false><<<nb, 32 * WPB, 0, s>>>(m, pst);
         return cudaGetLastError();
@@ -1212,11 +1252,11 @@ cudaError_t launch_facet_pf(const DeviceModel &m, const void *pst, cudaStream_t 
 
 // Per-facet parameters matter only where the law or E0 / alpha enter: the step and the metrics.
 template <class R, int MODE>
-cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t s)
+cudaError_t launch_facet_tpb(const DeviceModel &m, const void *pst, cudaStream_t s, const BatchLaw *bl)
 {
     if constexpr (MODE == FACET_STEP || MODE == FACET_METRIC)
-        if (m.pf) return launch_facet_pf<R, MODE, true>(m, pst, s);
-    return launch_facet_pf<R, MODE, false>(m, pst, s);
+        if (m.pf) return launch_facet_pf<R, MODE, true>(m, pst, s, bl);
+    return launch_facet_pf<R, MODE, false>(m, pst, s, bl);
 }
 
 // Persistent launch of `nsteps` steps (cooperative; grid = resident blocks per SM x SMs).  Returns
@@ -1281,20 +1321,21 @@ cudaError_t launch_kick(const DeviceModel &m, cudaStream_t s)
 }
 
 template <class R>
-cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s)
+cudaError_t launch_facet(const DeviceModel &m, int mode, const void *src_override, cudaStream_t s,
+                         const BatchLaw *bl)
 {
     const void *pst = src_override ? src_override
                                    : (sizeof(R) == 4 ? static_cast<const void *>(m.pm32)
                                                      : static_cast<const void *>(m.pstate));
     switch (mode) {
     case FACET_FROM_HIST:
-        return launch_facet_tpb<R, FACET_FROM_HIST>(m, pst, s);
+        return launch_facet_tpb<R, FACET_FROM_HIST>(m, pst, s, bl);
     case FACET_ELASTIC:
-        return launch_facet_tpb<R, FACET_ELASTIC>(m, pst, s);
+        return launch_facet_tpb<R, FACET_ELASTIC>(m, pst, s, bl);
     case FACET_METRIC:
-        return launch_facet_tpb<R, FACET_METRIC>(m, pst, s);
+        return launch_facet_tpb<R, FACET_METRIC>(m, pst, s, bl);
     default:
-        return launch_facet_tpb<R, FACET_STEP>(m, pst, s);
+        return launch_facet_tpb<R, FACET_STEP>(m, pst, s, bl);
     }
 }
 
@@ -1380,8 +1421,8 @@ cudaError_t launch_persistent(const DeviceModel &m, int64_t nsteps, const Persis
 
 template cudaError_t launch_persistent<float>(const DeviceModel &, int64_t, const PersistCtl &, int *, cudaStream_t);
 template cudaError_t launch_persistent<double>(const DeviceModel &, int64_t, const PersistCtl &, int *, cudaStream_t);
-template cudaError_t launch_facet<float>(const DeviceModel &, int, const void *, cudaStream_t);
-template cudaError_t launch_facet<double>(const DeviceModel &, int, const void *, cudaStream_t);
+template cudaError_t launch_facet<float>(const DeviceModel &, int, const void *, cudaStream_t, const BatchLaw *);
+template cudaError_t launch_facet<double>(const DeviceModel &, int, const void *, cudaStream_t, const BatchLaw *);
 template cudaError_t launch_gather<float>(const DeviceModel &, int, double *, cudaStream_t);
 template cudaError_t launch_gather<double>(const DeviceModel &, int, double *, cudaStream_t);
 template cudaError_t launch_hist_to_user<float>(const DeviceModel &, const int32_t *, int64_t, double *, cudaStream_t);

@@ -106,3 +106,29 @@ def test_full_size_batch_one_step_against_oracle():
         assert stg == st + 1
         assert nrel(qg, qo) <= 2e-5 and nrel(vg, vo) <= 2e-5, (i, nrel(qg, qo), nrel(vg, vo))
     b.close()
+
+
+def test_law_constants_in_parameters_and_beyond():
+    """Mixed-mode batches of up to 64 specimens take the law constants from the facet pass's kernel
+    parameters (each block finds its specimen from its index), larger ones from device memory: both
+    give every specimen its separate run bit for bit, at the boundary (64 and 65 specimens)."""
+    specs = [specimen.make_cube_specimen(8.0, 2.0, 4.0, 80, seed=100 + i) for i in range(65)]
+    bcs = [workloads.unconfined_compression_bc(s, velocity=300.0, ramp_time=1e-5) for s in specs]
+    mats = [dict(MAT, sigma_t=3.0 + 0.02 * i) for i in range(65)]
+    dts = [1.0e-7 * (1.0 + 0.001 * i) for i in range(65)]
+    singles = {}
+    for n in (64, 65):
+        b = ldpm.Batch(specs[:n], mats[:n], "mixed", dts=dts[:n], bcs=bcs[:n])
+        b.step(60)
+        for i in (0, 31, n - 1):
+            if i not in singles:
+                m = ldpm.Model(specs[i], mats[i], precision="mixed", dt=dts[i], bc=bcs[i])
+                m.step(60)
+                singles[i] = (m.get_state(), m.energy())
+                m.close()
+            (ss, (es, rs)), sb = singles[i], b.get_state(i)
+            for x, y in zip(sb[:3], ss[:3]):
+                assert np.array_equal(x, y), (n, i)
+            eb, rb = b.energy(i)
+            assert np.array_equal(eb, es) and np.array_equal(rb, rs), (n, i)
+        b.close()
