@@ -71,10 +71,13 @@ def gather_pass_bytes(T: int, N: int, r: int) -> float:
     return T * 4 * 6 * r + N * (SLOT_TABLE_BYTES + 4 + 192 + 128 + 64 + (84 if r == 4 else 0))
 
 
-def kernel_src_hash() -> str:
-    """Hash of the kernel sources and of the build script (its compiler flags shape the kernels)."""
+def kernel_src_hash(kernel: str = "facet_warp_kernel") -> str:
+    """Hash of the sources a kernel is compiled from (its translation unit, the shared device header
+    and internal layout) and of the build script (its compiler flags shape the kernel): the reverse
+    passes live in ldpm_adjoint.cu, every other kernel in ldpm_kernels.cu."""
+    unit = "ldpm_adjoint.cu" if kernel.startswith("adjoint_") else "ldpm_kernels.cu"
     h = hashlib.sha256()
-    for f in ("ldpm_kernels.cu", "ldpm_adjoint.cu", "ldpm_device.cuh", "ldpm_internal.h"):
+    for f in (unit, "ldpm_device.cuh", "ldpm_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "csrc", f), "rb").read())
     h.update(open(os.path.join(ROOT, "paper_2603_13190_gb300", "build.py"), "rb").read())
     return h.hexdigest()[:16]
@@ -97,7 +100,7 @@ def recorded_traffic(kernel: str, workload: str, prec: str, field: str = "bytes_
     try:
         d = json.load(open(p))
         e = d.get("%s/%s/%s" % (kernel, workload, prec))
-        if e and e.get("kernel_src_hash") == kernel_src_hash() and field in e:
+        if e and e.get("kernel_src_hash") == kernel_src_hash(kernel) and field in e:
             return float(e[field])
     except Exception:
         return None

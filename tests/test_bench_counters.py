@@ -28,17 +28,17 @@ def test_counters_follow_the_per_unit_formulas():
 
 
 def test_recorded_traffic_is_tied_to_the_kernel_source(monkeypatch):
-    """`traffic` in the bench line comes from profiles/traffic.json only while the kernel sources hash
-    to the value the capture was taken with; any other source reads as null."""
+    """`traffic` in the bench line comes from profiles/traffic.json only while the sources of the
+    recorded kernel hash to the value the capture was taken with; any other source reads as null."""
     import json
 
     d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
     key = "facet_warp_kernel/uniaxial_tension/mixed"
     assert key in d and d[key]["bytes_per_launch"] > 0
-    monkeypatch.setattr(bench, "kernel_src_hash", lambda: d[key]["kernel_src_hash"])
+    monkeypatch.setattr(bench, "kernel_src_hash", lambda kernel="": d[key]["kernel_src_hash"])
     assert bench.recorded_traffic("facet_warp_kernel", "uniaxial_tension", "mixed") == d[key]["bytes_per_launch"]
     assert bench.recorded_traffic("no_such_kernel", "uniaxial_tension", "mixed") is None
-    monkeypatch.setattr(bench, "kernel_src_hash", lambda: "0" * 16)
+    monkeypatch.setattr(bench, "kernel_src_hash", lambda kernel="": "0" * 16)
     assert bench.recorded_traffic("facet_warp_kernel", "uniaxial_tension", "mixed") is None
     assert bench.fp64_alu_roofline("uniaxial_tension", 1.5) is None
 
@@ -96,3 +96,14 @@ def test_fp64_alu_roofline_needs_a_count_of_the_same_workload(monkeypatch):
     r = bench.fp64_alu_roofline("confined_compression", 5.0, facets=12535080, sm_count=148, sm_mhz=2000.0)
     assert abs(r["flop_per_launch"] - 12535080 * 300.0) < 1e-3 and r["flops"] == "counted on this workload"
     assert abs(r["peak"] - 148 * 2 * 2 * 2.0e9 / 1e12) < 1e-12 and "148 SMs" in r["peak_source"]
+
+
+def test_every_recorded_count_belongs_to_the_current_sources():
+    """The committed DRAM traffic and FP64 flop counts were taken on the kernels as they are: each
+    entry's hash is that of its kernel's current sources and build flags."""
+    import json
+
+    d = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    assert d
+    for key, e in d.items():
+        assert e["kernel_src_hash"] == bench.kernel_src_hash(key.split("/")[0]), key
