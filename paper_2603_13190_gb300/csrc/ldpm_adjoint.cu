@@ -341,10 +341,11 @@ constexpr int kAPlane = 6 * 4 * kATets + 2;
 
 // Mixed mode: 8 resident blocks per SM.  The register cap (80 per thread) costs 24 bytes of spills
 // and doubles the occupancy of the uncapped build; measured 10 % faster on GB300.  The FP64 build
-// (bound by the FP64 pipe) keeps its registers.
-template <class R, bool KT>
-__global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_facet_kernel(DeviceModel m,
-                                                                                            AdjointModel a)
+// (bound by the FP64 pipe) keeps its registers.  S1: one specimen in mixed mode, law constants from
+// the kernel parameters (m.law1) instead of the global array, as in the forward facet pass.
+template <class R, bool KT, bool S1>
+__global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1)
+    adjoint_facet_kernel(const __grid_constant__ DeviceModel m, AdjointModel a)
 {
     using T4 = R4<R>;
     constexpr int TETS = kATets;
@@ -539,10 +540,16 @@ __global__ void __launch_bounds__(12 * kATets, sizeof(R) == 4 ? 8 : 1) adjoint_f
         tangent_frame(n, mt, lt);
         const V3<R> ca = {g.x, g.y, g.z};
         const V3<R> cb = ca - d;
-        const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;
+        const LawConst<R> *lbase;
+        if constexpr (S1 && sizeof(R) == 4) {
+            lbase = reinterpret_cast<const LawConst<R> *>(&m.law1);
+        } else {
+            const int sp = m.tile_spec ? m.tile_spec[tet0 / 32] : 0;
+            lbase = lawc + sp;
+        }
         LawConst<R> cpf;
-        if (m.pf) cpf = facet_params(lawc[sp], pp.x, pp.y, pp.z);
-        const LawConst<R> &c = m.pf ? cpf : lawc[sp];
+        if (m.pf) cpf = facet_params(*lbase, pp.x, pp.y, pp.z);
+        const LawConst<R> &c = m.pf ? cpf : *lbase;
         const V3<R> thA = {A[9], A[10], A[11]}, thB = {B[9], B[10], B[11]};
         const V3<R> du = {B[3] - A[3], B[4] - A[4], B[5] - A[5]};
         const V3<R> jump = du + cross(thB, cb) - cross(thA, ca);
@@ -863,10 +870,18 @@ cudaError_t launch_adjoint_facet(const DeviceModel &m, const AdjointModel &a, cu
 {
     const unsigned fblocks = (unsigned)((m.T + kATets - 1) / kATets);
     if (fblocks) {
-        if (a.reload)
-            adjoint_facet_kernel<R, true><<<fblocks, 12 * kATets, 0, s>>>(m, a);
-        else
-            adjoint_facet_kernel<R, false><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+        const bool s1 = sizeof(R) == 4 && m.n_spec == 1;
+        if (a.reload) {
+            if (s1)
+                adjoint_facet_kernel<R, true, true><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+            else
+                adjoint_facet_kernel<R, true, false><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+        } else {
+            if (s1)
+                adjoint_facet_kernel<R, false, true><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+            else
+                adjoint_facet_kernel<R, false, false><<<fblocks, 12 * kATets, 0, s>>>(m, a);
+        }
     }
     return cudaGetLastError();
 }
