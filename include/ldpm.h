@@ -48,12 +48,13 @@ typedef struct ldpm_ctx *ldpm_t; /* opaque handle, owned by the library */
 
 typedef enum {
     LDPM_FP64 = 0,  /* every stage in FP64 */
-    LDPM_MIXED = 1  /* facet kinematics, constitutive law and facet forces in FP32, as is the sum of
-                       each tetrahedron's 6 facet terms at one of its vertices; the particle sums of
-                       those shares (Eq. (2a)-(2b)) and the energy increments (trapezoid products
-                       and their 6-DOF sums, Sec. 4) in compensated float-float arithmetic (48-bit
-                       significand, on the FP32 pipe); particle state, velocity update and the
-                       energy accumulators in FP64 */
+    LDPM_MIXED = 1  /* facet kinematics, constitutive law and facet forces in FP32 (subnormal FP32
+                       values flushed to zero), as is the sum of each tetrahedron's 6 facet terms at
+                       one of its vertices; the particle sums of those shares (Eq. (2a)-(2b)) and
+                       the energy increments (products with the half-step velocity and their 6-DOF
+                       sums, Sec. 4) in compensated float-float arithmetic (48-bit significand, on
+                       the FP32 pipe); particle state, velocity update, the increments' factor dt/2
+                       and the energy accumulators in FP64 */
 } ldpm_precision;
 
 /* Raw specimen geometry (paper Sec. 3.1: particles, Delaunay tetrahedra, 12 facets per
